@@ -1,0 +1,359 @@
+"""Coupling-step benchmark: Lagrangian nodes coupled per second on the dense
+blood suspension (500 RBC + 100 platelets, 1.33M nodes, 256^3 periodic MAC
+grid), FP32, through the C ABI of libifem.
+
+One step = node binning + element forces (membrane Skalak + Helfrich bending,
+platelet neo-Hookean tets) + spreading + interpolation + FP64 conservation
+sums, replayed from a CUDA graph. Inputs are resident in HBM; L2 (129 MB) is
+flushed between timed steps by writing a 256 MB buffer.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ifem|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+repository) on the same workload, on the host cores.
+Under torchrun (N > 1) every rank runs its own replica of the workload (the
+step has no cross-rank exchange); value = all ranks' nodes / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Lagrangian nodes coupled/s (force+spread+interp) and HBM GB/s; FP32-batched vs FP64 at stated err"
+WORKLOAD = ("dense blood suspension: 500 RBC (2562 nodes, Skalak C=100 + bending) + 100 platelets "
+            "(512 nodes / 2058 tets, NH), 256^3 periodic MAC grid, Ht 0.20, 4-point delta")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [s.strip() for s in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(N, T, P, real=4):
+    """Algorithmic bytes per stage (measurement section).
+
+    N nodes, T touched lattice values (3 lattices), P (tile, node) pairs."""
+    return {
+        "bin": 2 * 3 * real * N + 4 * (N + P),          # x read (count + fill), pair/own lists written
+        "forces": 2 * 3 * real * N,                     # x read, F written
+        "spread": 2 * 3 * real * N + 4 * P + 2 * real * T,  # x, F read; pair list read; f read + written
+        "interp": 2 * 3 * real * N + 4 * N + real * T,  # x read, v written, order list read; u read
+        "reduce": 3 * 3 * real * N,                     # x, F, v read
+        "step": 4 * 3 * real * N + 3 * real * T,        # x, v, F write + read; u read, f read + written
+    }
+
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle on the same workload (rank 0 only)."""
+    if rank != 0:
+        return
+    import ifem_workloads as W
+    from oracle import oracle as O
+    O.build()
+    wl = W.make("C4")
+    xl = wl.x_local_all(np.float32).astype(np.float64)
+    N = wl.n_nodes
+    # bounded sample: every `stride`-th particle, sized to a few seconds per step
+    stride = 4
+    sel = list(range(0, len(wl.instances), stride))
+    n_sel = int(sum(wl.templates[wl.instances[i].tmpl].n_nodes for i in sel))
+    for _ in range(max(0, args.warmup)):
+        O.oracle_step(wl, x_local=xl, instances=sel)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.oracle_step(wl, x_local=xl, instances=sel)
+        ts.append(time.perf_counter() - t0)
+    t = float(np.mean(ts))
+    val = n_sel / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "nodes/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": N, "grid": 256, "sample_nodes": n_sel},
+        "cpu_baseline": {"value": val, "unit": "nodes/s", "cores": 1, "kind": "oracle",
+                         "sample": f"every {stride}th particle of the suspension ({n_sel} nodes), one full "
+                                   "step (forces + spread + interp + sums) per timed step, single thread"},
+        "e2e": {"value": val, "unit": "nodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample(wl):
+    """Oracle timed on a bounded sample of the workload (host cores, one thread)."""
+    from oracle import oracle as O
+    O.build()
+    xl = wl.x_local_all(np.float32).astype(np.float64)
+    stride = 4
+    sel = list(range(0, len(wl.instances), stride))
+    n_sel = int(sum(wl.templates[wl.instances[i].tmpl].n_nodes for i in sel))
+    O.oracle_step(wl, x_local=xl, instances=sel[:2])
+    t0 = time.perf_counter()
+    O.oracle_step(wl, x_local=xl, instances=sel)
+    t = time.perf_counter() - t0
+    return {"value": n_sel / t, "unit": "nodes/s", "cores": 1, "kind": "oracle",
+            "sample": f"every 4th particle ({n_sel} nodes), one full step (forces + spread + interp + "
+                      f"sums), single thread, {t:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ifem", choices=["ifem", "reference"])
+    ap.add_argument("--scatter", default="atomic", choices=["atomic", "det"])
+    ap.add_argument("--tile", type=int, default=8)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import ifem_workloads as W
+    from paper_1807_08219_gb300 import ifem as I
+
+    wl = W.make("C4")
+    N = wl.n_nodes
+    scatter = I.IFEM_SCATTER_ATOMIC if args.scatter == "atomic" else I.IFEM_SCATTER_DET
+    cp = I.Coupler(wl, precision=I.IFEM_FP32, scatter=scatter, tile=args.tile, device=local)
+    dev = cp.device
+    xl32 = wl.x_local_all(np.float32)
+    x = cp.nodes_to_device(xl32)
+    u = cp.grid_to_device(wl.u)
+    F, v = cp.empty_nodes(), cp.empty_nodes()
+    f = cp.zeros_grid()
+    red = torch.zeros(12 * len(wl.instances) + 6, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def step(s):
+        I.ifem_step_coupling(cp.ctx, cp.batch, cp.grid, x, u, F, f, v, red, 0, s)
+
+    # first step outside capture: allocates the work buffers, gives the counts
+    with torch.cuda.stream(stream):
+        step(stream)
+    torch.cuda.synchronize()
+    _, st = I.ifem_sync_status(cp.ctx)
+    T, P = st["touched_cells"], st["pairs"]
+
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        step(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        g.replay()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times = []
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            g.replay()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall0
+    ck = clocks.stop()
+    t_ms = float(np.mean(times))
+    if dist:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = world * N / (t_ms * 1e-3)
+
+    # per-stage times of the same step (profiled context, same stream, same flush)
+    cpp = I.Coupler(wl, precision=I.IFEM_FP32, scatter=scatter, tile=args.tile, device=local, profile=1)
+    stages = {k: [] for k in ("bin", "forces", "spread", "interp", "reduce")}
+    fp = cpp.zeros_grid()
+    for it in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        with torch.cuda.stream(stream):
+            I.ifem_step_coupling(cpp.ctx, cpp.batch, cpp.grid, x, u, F, fp, v, red, 0, stream)
+        ms = I.ifem_stage_times(cpp.ctx)
+        if it >= args.warmup:
+            for k in stages:
+                stages[k].append(ms[k])
+    I.ifem_sync_status(cpp.ctx)
+    stage_ms = {k: float(np.mean(vv)) for k, vv in stages.items()}
+    cpp.close()
+    ab = algorithmic_bytes(N, T, P)
+    hbm, peak_kind = peaks()
+    dom = max(("spread", "interp", "forces", "bin"), key=lambda k: stage_ms[k])
+    achieved = ab[dom] / (stage_ms[dom] * 1e-3) / 1e9
+    step_gbs = ab["step"] / (t_ms * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers (pinned)
+    x_host = torch.from_numpy(np.ascontiguousarray(xl32.T)).pin_memory()
+    v_host = torch.empty((3, N), dtype=torch.float32).pin_memory()
+    red_host = torch.empty(red.numel(), dtype=torch.float64).pin_memory()
+    e2e = []
+    for it in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            x.copy_(x_host, non_blocking=True)
+            step(stream)
+            v_host.copy_(v, non_blocking=True)
+            red_host.copy_(red, non_blocking=True)
+            e1.record(stream)
+        e1.synchronize()
+        if it >= args.warmup:
+            e2e.append(e0.elapsed_time(e1))
+    e2e_ms = float(np.mean(e2e))
+    if dist:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+
+    # FP64 deterministic GPU path on the same workload (reported beside)
+    fp64 = None
+    if not args.no_fp64:
+        c64 = I.Coupler(wl, precision=I.IFEM_FP64, tile=args.tile, device=local)
+        x64 = c64.nodes_to_device(xl32.astype(np.float64))
+        u64 = c64.grid_to_device(wl.u)
+        F64, v64, f64 = c64.empty_nodes(), c64.empty_nodes(), c64.zeros_grid()
+        for _ in range(2):
+            I.ifem_step_coupling(c64.ctx, c64.batch, c64.grid, x64, u64, F64, f64, v64, None, 0, stream)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            I.ifem_step_coupling(c64.ctx, c64.batch, c64.grid, x64, u64, F64, f64, v64, None, 0, stream)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        I.ifem_sync_status(c64.ctx)
+        # error of the FP32 step against the FP64 GPU step (same inputs)
+        Fd = F.double()
+        vd = v.double()
+        eF = float(torch.linalg.norm(Fd - F64) / torch.linalg.norm(F64))
+        ev = float(torch.linalg.norm(vd - v64) / torch.linalg.norm(v64))
+        t64 = float(np.mean(ts))
+        fp64 = {"value": N / (t64 * 1e-3), "unit": "nodes/s", "ms_per_step": t64,
+                "fp32_rel_l2_vs_fp64": {"F": eF, "v": ev}}
+        c64.close()
+
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu else cpu_baseline_sample(wl)
+    launches_per_step = 5 + 1 + 1 + 1 + 2  # bin (count, 3 scan, fill), forces, spread, interp, 2 reductions
+    if scatter == I.IFEM_SCATTER_DET:
+        launches_per_step += 3
+    line = {
+        "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": N, "particles": len(wl.instances), "grid": 256,
+                   "kernel": "peskin4", "scatter": args.scatter, "tile": args.tile, "cuda_graph": True,
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "hbm_gbs_step": step_gbs,
+        "step_roofline_frac": step_gbs / hbm,
+        "stage_ms": stage_ms,
+        "touched_values": T, "pairs": P,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                     "algorithmic_bytes": ab[dom]},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * N / (e2e_ms * 1e-3), "unit": "nodes/s", "h2d_bytes_per_step": 12 * N,
+                "d2h_bytes_per_step": 12 * N + 8 * red.numel()},
+        "fp64": fp64,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": ck,
+        "wall_s_timed": wall,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

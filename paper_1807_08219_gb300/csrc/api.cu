@@ -1,0 +1,930 @@
+// api.cu -- the extern "C" entry points of libifem (declared in ifem.h):
+// handle management, host-side argument checks, FP64 reference data of the
+// templates, work-buffer sizing and the launch sequences of the coupling
+// step. Host code here is compiled with -ffp-contract=off so that the FP64
+// reference invariants follow the exact evaluation order written below.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <set>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/ifem.h"
+#include "common.cuh"
+
+using namespace ifem;
+
+struct ifem_ctx_s {
+    ifem_config cfg;
+    int n_sm = 0;
+    int tile = 8;
+    std::string err;
+    unsigned long long *d_status = nullptr;
+    unsigned long long *h_status = nullptr;
+    cudaEvent_t ev[6] = {};
+    int ev_ok = 0;
+    int ev_recorded = 0;
+};
+
+struct ifem_tmpl_s {
+    ifem_ctx ctx;
+    int kind;  // 0 membrane, 1 solid
+    int law;
+    int n_nodes, n_elems;
+    double mu, C, kb, c0, lam;
+    int *d_elems = nullptr;
+    double *d_ref_d = nullptr;
+    float *d_ref_f = nullptr;
+    int *d_inc_off = nullptr;
+    int *d_inc_idx = nullptr;
+};
+
+struct ifem_grid_s {
+    ifem_ctx ctx;
+    int n_boxes;
+    std::vector<int> n;
+    std::vector<double> L;
+    std::vector<long long> off;
+    long long total;
+};
+
+struct Workspace {
+    ifem_grid grid = nullptr;
+    int tile = 0;
+    long long n_tiles = 0;
+    int max_edge = 0;
+    BoxDev *d_boxes = nullptr;
+    DevWork w{};
+    std::vector<void *> allocs;
+};
+
+struct ifem_batch_s {
+    ifem_ctx ctx;
+    std::vector<ifem_tmpl> tmpls;
+    std::vector<ifem_instance_desc> inst;
+    std::vector<InstDev> h_inst;
+    long long N = 0;
+    long long n_elems = 0;
+    int max_nodes = 0, max_elems = 0;
+    int any_bending = 0, fused_ok = 0;
+    int max_box = 0;
+    ifem_grid grid0 = nullptr;
+    InstDev *d_inst = nullptr;
+    TmplDev *d_tmpl = nullptr;
+    int *d_node_inst = nullptr;
+    void *d_elem_buf = nullptr;
+    void *d_bend_buf = nullptr;
+    Workspace ws;
+};
+
+// ------------------------------------------------------------ helpers
+static int fail(ifem_ctx ctx, int code, const std::string &msg)
+{
+    if (ctx)
+        ctx->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? IFEM_ERR_OOM : IFEM_ERR_CUDA,      \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                      \
+    } while (0)
+
+template <typename T>
+static cudaError_t upload(T **dst, const T *src, size_t n)
+{
+    *dst = nullptr;
+    if (n == 0)
+        return cudaSuccess;
+    cudaError_t e = cudaMalloc((void **)dst, sizeof(T) * n);
+    if (e != cudaSuccess)
+        return e;
+    return cudaMemcpy(*dst, src, sizeof(T) * n, cudaMemcpyHostToDevice);
+}
+
+static size_t real_size(ifem_ctx ctx) { return ctx->cfg.precision == IFEM_FP64 ? 8 : 4; }
+
+// ------------------------------------------------------------ context
+extern "C" int ifem_config_default(ifem_config *cfg)
+{
+    if (!cfg)
+        return IFEM_ERR_ARG;
+    cfg->precision = IFEM_FP32;
+    cfg->kernel = IFEM_KERNEL_PESKIN4;
+    cfg->scatter = IFEM_SCATTER_DET;
+    cfg->tile = 0;
+    cfg->mls_support = 0.0;
+    cfg->device = 0;
+    cfg->profile = 0;
+    return IFEM_OK;
+}
+
+extern "C" int ifem_ctx_create(const ifem_config *cfg, ifem_ctx *out)
+{
+    ifem_ctx ctx = nullptr;
+    if (!cfg || !out)
+        return IFEM_ERR_ARG;
+    *out = nullptr;
+    if (cfg->precision != IFEM_FP32 && cfg->precision != IFEM_FP64)
+        return IFEM_ERR_ARG;
+    if (cfg->kernel != IFEM_KERNEL_PESKIN4 && cfg->kernel != IFEM_KERNEL_MLS27)
+        return IFEM_ERR_ARG;
+    if (cfg->scatter != IFEM_SCATTER_DET && cfg->scatter != IFEM_SCATTER_ATOMIC)
+        return IFEM_ERR_ARG;
+    if (cfg->tile != 0 && (cfg->tile < 6 || cfg->tile > 16))
+        return IFEM_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev)
+        return IFEM_ERR_CUDA;
+    ctx = new ifem_ctx_s();
+    ctx->cfg = *cfg;
+    if (!(ctx->cfg.mls_support > 0.0))
+        ctx->cfg.mls_support = std::sqrt(3.0);
+    ctx->tile = cfg->tile ? cfg->tile : 8;
+    if (cudaSetDevice(cfg->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, cfg->device) != cudaSuccess ||
+        cudaMalloc((void **)&ctx->d_status, sizeof(unsigned long long) * kStatusWords) != cudaSuccess ||
+        cudaMemset(ctx->d_status, 0, sizeof(unsigned long long) * kStatusWords) != cudaSuccess ||
+        cudaMallocHost((void **)&ctx->h_status, sizeof(unsigned long long) * kStatusWords) != cudaSuccess) {
+        if (ctx->d_status)
+            cudaFree(ctx->d_status);
+        delete ctx;
+        return IFEM_ERR_CUDA;
+    }
+    if (cfg->profile) {
+        ctx->ev_ok = 1;
+        for (int i = 0; i < 6; ++i)
+            if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess)
+                ctx->ev_ok = 0;
+    }
+    *out = ctx;
+    return IFEM_OK;
+}
+
+extern "C" int ifem_ctx_destroy(ifem_ctx ctx)
+{
+    if (!ctx)
+        return IFEM_ERR_ARG;
+    for (int i = 0; i < 6; ++i)
+        if (ctx->ev[i])
+            cudaEventDestroy(ctx->ev[i]);
+    cudaFree(ctx->d_status);
+    cudaFreeHost(ctx->h_status);
+    delete ctx;
+    return IFEM_OK;
+}
+
+extern "C" const char *ifem_last_error(ifem_ctx ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" int ifem_ctx_tile(ifem_ctx ctx) { return ctx ? ctx->tile : IFEM_ERR_ARG; }
+
+extern "C" int ifem_stage_times(ifem_ctx ctx, double *ms)
+{
+    if (!ctx || !ms || !ctx->ev_ok || !ctx->ev_recorded)
+        return fail(ctx, IFEM_ERR_ARG, "stage_times: profiling off or no step recorded");
+    CK(cudaEventSynchronize(ctx->ev[5]));
+    for (int i = 0; i < 5; ++i) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, ctx->ev[i], ctx->ev[i + 1]));
+        ms[i] = t;
+    }
+    return IFEM_OK;
+}
+
+static void mark(ifem_ctx ctx, int i, void *stream)
+{
+    if (ctx->ev_ok)
+        cudaEventRecord(ctx->ev[i], (cudaStream_t)stream);
+}
+
+extern "C" int ifem_sync_status(ifem_ctx ctx, ifem_stats *out)
+{
+    if (!ctx)
+        return IFEM_ERR_ARG;
+    CK(cudaSetDevice(ctx->cfg.device));
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(ctx->h_status, ctx->d_status, sizeof(unsigned long long) * kStatusWords, cudaMemcpyDeviceToHost));
+    CK(cudaMemset(ctx->d_status, 0, sizeof(unsigned long long) * kStatusWords));
+    const unsigned long long *s = ctx->h_status;
+    if (out) {
+        out->inverted_elements = (int64_t)s[ST_INVERTED];
+        out->domain_errors = (int64_t)s[ST_DOMAIN];
+        out->capacity_errors = (int64_t)s[ST_CAPACITY];
+        out->timeouts = (int64_t)s[ST_TIMEOUT];
+        out->pairs = (int64_t)s[ST_PAIRS];
+        out->active_tiles = (int64_t)s[ST_ACTIVE];
+        out->touched_cells = (int64_t)s[ST_TOUCHED];
+    }
+    if (s[ST_TIMEOUT])
+        return fail(ctx, IFEM_ERR_TIMEOUT, "a bounded device wait expired");
+    if (s[ST_DOMAIN])
+        return fail(ctx, IFEM_ERR_DOMAIN, "non-finite position or singular MLS moment matrix");
+    if (s[ST_CAPACITY])
+        return fail(ctx, IFEM_ERR_CAPACITY, "a per-tile list exceeded the deterministic kernels' limit");
+    if (s[ST_INVERTED])
+        return fail(ctx, IFEM_ERR_INVERTED, "inverted elements (J <= 0) were evaluated");
+    return IFEM_OK;
+}
+
+// ------------------------------------------------------------ templates
+// Membrane reference data per triangle (a, b, c), FP64, in this order:
+//   E1 = Xb - Xa, E2 = Xc - Xa; l1 = sqrt((E1x^2 + E1y^2) + E1z^2); e1 = E1 / l1;
+//   nr = E1 x E2; nl = sqrt((nrx^2 + nry^2) + nrz^2); nh = nr / nl; e2 = nh x e1;
+//   d01 = (e1x E2x + e1y E2y) + e1z E2z; d11 = (e2x E2x + e2y E2y) + e2z E2z;
+//   Dm^-1 = [1/l1, -d01/(l1*d11); 0, 1/d11]; A0 = 0.5*nl.
+static void membrane_reference(int nt, const int32_t *tri, const double *X, std::vector<double> &ref)
+{
+    ref.assign((size_t)nt * 5, 0.0);
+    for (int e = 0; e < nt; ++e) {
+        const double *Xa = X + 3 * tri[3 * e], *Xb = X + 3 * tri[3 * e + 1], *Xc = X + 3 * tri[3 * e + 2];
+        double E1[3], E2[3], e1[3], nr[3], nh[3], e2[3];
+        for (int i = 0; i < 3; ++i) {
+            E1[i] = Xb[i] - Xa[i];
+            E2[i] = Xc[i] - Xa[i];
+        }
+        double l1 = std::sqrt((E1[0] * E1[0] + E1[1] * E1[1]) + E1[2] * E1[2]);
+        for (int i = 0; i < 3; ++i)
+            e1[i] = E1[i] / l1;
+        nr[0] = E1[1] * E2[2] - E1[2] * E2[1];
+        nr[1] = E1[2] * E2[0] - E1[0] * E2[2];
+        nr[2] = E1[0] * E2[1] - E1[1] * E2[0];
+        double nl = std::sqrt((nr[0] * nr[0] + nr[1] * nr[1]) + nr[2] * nr[2]);
+        for (int i = 0; i < 3; ++i)
+            nh[i] = nr[i] / nl;
+        e2[0] = nh[1] * e1[2] - nh[2] * e1[1];
+        e2[1] = nh[2] * e1[0] - nh[0] * e1[2];
+        e2[2] = nh[0] * e1[1] - nh[1] * e1[0];
+        double d01 = (e1[0] * E2[0] + e1[1] * E2[1]) + e1[2] * E2[2];
+        double d11 = (e2[0] * E2[0] + e2[1] * E2[1]) + e2[2] * E2[2];
+        double *r = ref.data() + 5 * (size_t)e;
+        r[0] = 1.0 / l1;
+        r[1] = -d01 / (l1 * d11);
+        r[2] = 0.0;
+        r[3] = 1.0 / d11;
+        r[4] = 0.5 * nl;
+    }
+}
+
+// Solid reference data per tet: Dm = [X1-X0, X2-X0, X3-X0] (columns),
+// det by cofactors of row 0, Dm^-1 = adj(Dm)/det (rows = grad N_1..3),
+// V0 = det / 6.
+static bool tet_reference(int ne, const int32_t *tet, const double *X, std::vector<double> &ref)
+{
+    ref.assign((size_t)ne * 10, 0.0);
+    for (int e = 0; e < ne; ++e) {
+        const double *X0 = X + 3 * tet[4 * e];
+        double M[3][3];
+        for (int c = 0; c < 3; ++c) {
+            const double *Xc = X + 3 * tet[4 * e + 1 + c];
+            for (int i = 0; i < 3; ++i)
+                M[i][c] = Xc[i] - X0[i];
+        }
+        double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1])
+                   - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0])
+                   + M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+        if (!(det > 0.0))
+            return false;
+        double *r = ref.data() + 10 * (size_t)e;
+        r[0] = (M[1][1] * M[2][2] - M[1][2] * M[2][1]) / det;
+        r[1] = (M[0][2] * M[2][1] - M[0][1] * M[2][2]) / det;
+        r[2] = (M[0][1] * M[1][2] - M[0][2] * M[1][1]) / det;
+        r[3] = (M[1][2] * M[2][0] - M[1][0] * M[2][2]) / det;
+        r[4] = (M[0][0] * M[2][2] - M[0][2] * M[2][0]) / det;
+        r[5] = (M[0][2] * M[1][0] - M[0][0] * M[1][2]) / det;
+        r[6] = (M[1][0] * M[2][1] - M[1][1] * M[2][0]) / det;
+        r[7] = (M[0][1] * M[2][0] - M[0][0] * M[2][1]) / det;
+        r[8] = (M[0][0] * M[1][1] - M[0][1] * M[1][0]) / det;
+        r[9] = det / 6.0;
+    }
+    return true;
+}
+
+// Node -> (element*4 + local vertex) incidence, ascending element id.
+static void incidence(int nn, int ne, int nv, const int32_t *el, std::vector<int> &off, std::vector<int> &idx)
+{
+    off.assign(nn + 1, 0);
+    for (int e = 0; e < ne; ++e)
+        for (int v = 0; v < nv; ++v)
+            off[el[nv * e + v] + 1]++;
+    for (int i = 0; i < nn; ++i)
+        off[i + 1] += off[i];
+    idx.assign(off[nn], 0);
+    std::vector<int> cur(off.begin(), off.end() - 1);
+    for (int e = 0; e < ne; ++e)
+        for (int v = 0; v < nv; ++v)
+            idx[cur[el[nv * e + v]]++] = e * 4 + v;
+}
+
+static int tmpl_upload(ifem_ctx ctx, ifem_tmpl t, int nv, const int32_t *el, const std::vector<double> &ref)
+{
+    std::vector<float> reff(ref.begin(), ref.end());
+    std::vector<int> off, idx;
+    incidence(t->n_nodes, t->n_elems, nv, el, off, idx);
+    CK(upload(&t->d_elems, el, (size_t)t->n_elems * nv));
+    CK(upload(&t->d_ref_d, ref.data(), ref.size()));
+    CK(upload(&t->d_ref_f, reff.data(), reff.size()));
+    CK(upload(&t->d_inc_off, off.data(), off.size()));
+    CK(upload(&t->d_inc_idx, idx.data(), idx.size()));
+    return IFEM_OK;
+}
+
+static int check_elems(int nn, int ne, int nv, const int32_t *el)
+{
+    for (long long i = 0; i < (long long)ne * nv; ++i)
+        if (el[i] < 0 || el[i] >= nn)
+            return 0;
+    for (int e = 0; e < ne; ++e)
+        for (int a = 0; a < nv; ++a)
+            for (int b = a + 1; b < nv; ++b)
+                if (el[nv * e + a] == el[nv * e + b])
+                    return 0;
+    return 1;
+}
+
+extern "C" int ifem_tmpl_create_membrane(ifem_ctx ctx, int n_nodes, int n_tris, const int32_t *tris,
+                                         const double *X_ref, int law, const ifem_membrane_params *p,
+                                         ifem_tmpl *out)
+{
+    if (!ctx || !out || !tris || !X_ref || !p || n_nodes < 3 || n_tris < 1)
+        return fail(ctx, IFEM_ERR_ARG, "membrane template: null pointer or empty mesh");
+    *out = nullptr;
+    if (law != IFEM_LAW_NEO_HOOKE && law != IFEM_LAW_SKALAK)
+        return fail(ctx, IFEM_ERR_ARG, "membrane template: unknown law");
+    if (!check_elems(n_nodes, n_tris, 3, tris))
+        return fail(ctx, IFEM_ERR_ARG, "membrane template: node index out of range or repeated");
+    if (p->kb != 0.0) {
+        // bending needs a closed 2-manifold: every edge shared by exactly two triangles
+        std::map<std::pair<int, int>, int> edges;
+        for (int e = 0; e < n_tris; ++e)
+            for (int c = 0; c < 3; ++c) {
+                int a = tris[3 * e + c], b = tris[3 * e + (c + 1) % 3];
+                edges[{std::min(a, b), std::max(a, b)}]++;
+            }
+        for (auto &kv : edges)
+            if (kv.second != 2)
+                return fail(ctx, IFEM_ERR_ARG, "membrane template: bending needs a closed surface");
+    }
+    std::vector<double> ref;
+    membrane_reference(n_tris, tris, X_ref, ref);
+    for (int e = 0; e < n_tris; ++e)
+        if (!(ref[5 * (size_t)e + 4] > 0.0) || !std::isfinite(ref[5 * (size_t)e + 1]))
+            return fail(ctx, IFEM_ERR_ARG, "membrane template: degenerate reference triangle");
+    ifem_tmpl t = new ifem_tmpl_s();
+    t->ctx = ctx;
+    t->kind = 0;
+    t->law = law;
+    t->n_nodes = n_nodes;
+    t->n_elems = n_tris;
+    t->mu = p->mu;
+    t->C = p->C;
+    t->kb = p->kb;
+    t->c0 = p->c0;
+    t->lam = 0.0;
+    CK(cudaSetDevice(ctx->cfg.device));
+    int rc = tmpl_upload(ctx, t, 3, tris, ref);
+    if (rc != IFEM_OK) {
+        ifem_tmpl_destroy(t);
+        return rc;
+    }
+    *out = t;
+    return IFEM_OK;
+}
+
+extern "C" int ifem_tmpl_create_solid(ifem_ctx ctx, int n_nodes, int n_tets, const int32_t *tets,
+                                      const double *X_ref, const ifem_solid_params *p, ifem_tmpl *out)
+{
+    if (!ctx || !out || !tets || !X_ref || !p || n_nodes < 4 || n_tets < 1)
+        return fail(ctx, IFEM_ERR_ARG, "solid template: null pointer or empty mesh");
+    *out = nullptr;
+    if (!check_elems(n_nodes, n_tets, 4, tets))
+        return fail(ctx, IFEM_ERR_ARG, "solid template: node index out of range or repeated");
+    std::vector<double> ref;
+    if (!tet_reference(n_tets, tets, X_ref, ref))
+        return fail(ctx, IFEM_ERR_ARG, "solid template: a reference tet has det <= 0");
+    ifem_tmpl t = new ifem_tmpl_s();
+    t->ctx = ctx;
+    t->kind = 1;
+    t->law = 0;
+    t->n_nodes = n_nodes;
+    t->n_elems = n_tets;
+    t->mu = p->mu;
+    t->C = 0.0;
+    t->kb = 0.0;
+    t->c0 = 0.0;
+    t->lam = p->lambda;
+    CK(cudaSetDevice(ctx->cfg.device));
+    int rc = tmpl_upload(ctx, t, 4, tets, ref);
+    if (rc != IFEM_OK) {
+        ifem_tmpl_destroy(t);
+        return rc;
+    }
+    *out = t;
+    return IFEM_OK;
+}
+
+extern "C" int ifem_tmpl_destroy(ifem_tmpl t)
+{
+    if (!t)
+        return IFEM_ERR_ARG;
+    cudaFree(t->d_elems);
+    cudaFree(t->d_ref_d);
+    cudaFree(t->d_ref_f);
+    cudaFree(t->d_inc_off);
+    cudaFree(t->d_inc_idx);
+    delete t;
+    return IFEM_OK;
+}
+
+// ------------------------------------------------------------ grid
+extern "C" int ifem_grid_create(ifem_ctx ctx, int n_boxes, const int32_t *n, const double *L, ifem_grid *out)
+{
+    if (!ctx || !out || !n || !L || n_boxes < 1)
+        return fail(ctx, IFEM_ERR_ARG, "grid: null pointer or no boxes");
+    *out = nullptr;
+    for (int b = 0; b < n_boxes; ++b)
+        if (n[b] < 8 || n[b] > 1024 || !(L[b] > 0.0) || !std::isfinite(L[b]))
+            return fail(ctx, IFEM_ERR_ARG, "grid: box sides must be 8..1024 cells with L > 0");
+    ifem_grid g = new ifem_grid_s();
+    g->ctx = ctx;
+    g->n_boxes = n_boxes;
+    g->n.assign(n, n + n_boxes);
+    g->L.assign(L, L + n_boxes);
+    g->off.resize(n_boxes);
+    long long tot = 0;
+    for (int b = 0; b < n_boxes; ++b) {
+        g->off[b] = tot;
+        tot += 3LL * n[b] * n[b] * n[b];
+    }
+    g->total = tot;
+    *out = g;
+    return IFEM_OK;
+}
+
+extern "C" int ifem_grid_destroy(ifem_grid g)
+{
+    if (!g)
+        return IFEM_ERR_ARG;
+    delete g;
+    return IFEM_OK;
+}
+
+extern "C" int64_t ifem_grid_values(ifem_grid g) { return g ? g->total : -1; }
+extern "C" int64_t ifem_grid_box_offset(ifem_grid g, int b)
+{
+    return (g && b >= 0 && b < g->n_boxes) ? g->off[b] : -1;
+}
+
+// ------------------------------------------------------------ batch
+static void split_origins(ifem_batch b, ifem_grid g)
+{
+    for (size_t i = 0; i < b->h_inst.size(); ++i) {
+        InstDev &I = b->h_inst[i];
+        double inv_h = (double)g->n[I.box] / g->L[I.box];
+        for (int a = 0; a < 3; ++a) {
+            double s0 = I.origin[a] * inv_h;
+            double fl = std::floor(s0);
+            I.I0[a] = (int)((long long)fl % g->n[I.box]);
+            I.f0[a] = (float)(s0 - fl);
+        }
+    }
+}
+
+extern "C" int ifem_batch_create(ifem_ctx ctx, int n_tmpl, const ifem_tmpl *tmpls, int n_inst,
+                                 const ifem_instance_desc *inst, ifem_grid grid, ifem_batch *out)
+{
+    if (!ctx || !out || !tmpls || n_tmpl < 1 || n_inst < 0 || (n_inst > 0 && !inst) || !grid)
+        return fail(ctx, IFEM_ERR_ARG, "batch: null pointer or bad counts");
+    *out = nullptr;
+    if (n_inst > 65535)
+        return fail(ctx, IFEM_ERR_CAPACITY, "batch: at most 65535 instances");
+    for (int t = 0; t < n_tmpl; ++t)
+        if (!tmpls[t] || tmpls[t]->ctx != ctx)
+            return fail(ctx, IFEM_ERR_ARG, "batch: template from another context");
+    ifem_batch b = new ifem_batch_s();
+    b->ctx = ctx;
+    b->tmpls.assign(tmpls, tmpls + n_tmpl);
+    b->inst.assign(inst, inst + n_inst);
+    b->grid0 = grid;
+    long long N = 0, E = 0;
+    std::vector<int> node_inst;
+    for (int i = 0; i < n_inst; ++i) {
+        const ifem_instance_desc &d = inst[i];
+        if (d.tmpl < 0 || d.tmpl >= n_tmpl || d.box < 0 || d.box >= grid->n_boxes ||
+            !std::isfinite(d.origin[0]) || !std::isfinite(d.origin[1]) || !std::isfinite(d.origin[2])) {
+            delete b;
+            return fail(ctx, IFEM_ERR_ARG, "batch: instance with bad template, box or origin");
+        }
+        ifem_tmpl t = tmpls[d.tmpl];
+        InstDev I{};
+        I.tmpl = d.tmpl;
+        I.box = d.box;
+        I.node_off = (int)N;
+        I.n_nodes = t->n_nodes;
+        I.elem_off = E;
+        I.n_elems = t->n_elems;
+        for (int a = 0; a < 3; ++a)
+            I.origin[a] = d.origin[a];
+        b->h_inst.push_back(I);
+        node_inst.insert(node_inst.end(), t->n_nodes, i);
+        N += t->n_nodes;
+        E += t->n_elems;
+        b->max_nodes = std::max(b->max_nodes, t->n_nodes);
+        b->max_elems = std::max(b->max_elems, t->n_elems);
+        b->max_box = std::max(b->max_box, d.box);
+        if (t->kind == 0 && t->kb != 0.0)
+            b->any_bending = 1;
+    }
+    if (N >= (1LL << 31)) {
+        delete b;
+        return fail(ctx, IFEM_ERR_CAPACITY, "batch: more than 2^31 - 1 nodes");
+    }
+    b->N = N;
+    b->n_elems = E;
+    b->fused_ok = fused_smem_bytes(b->max_nodes) <= (size_t)kFusedMaxSmemBytes;
+    split_origins(b, grid);
+    std::vector<TmplDev> td(n_tmpl);
+    for (int t = 0; t < n_tmpl; ++t) {
+        ifem_tmpl s = tmpls[t];
+        TmplDev &d = td[t];
+        d.kind = s->kind;
+        d.law = s->law;
+        d.n_nodes = s->n_nodes;
+        d.n_elems = s->n_elems;
+        d.elems = s->d_elems;
+        d.ref_d = s->d_ref_d;
+        d.ref_f = s->d_ref_f;
+        d.inc_off = s->d_inc_off;
+        d.inc_idx = s->d_inc_idx;
+        d.mu = s->mu;
+        d.C = s->C;
+        d.kb = s->kb;
+        d.c0 = s->c0;
+        d.lam = s->lam;
+    }
+    cudaSetDevice(ctx->cfg.device);
+    size_t rs = real_size(ctx);
+    if (upload(&b->d_tmpl, td.data(), td.size()) != cudaSuccess ||
+        upload(&b->d_inst, b->h_inst.data(), b->h_inst.size()) != cudaSuccess ||
+        upload(&b->d_node_inst, node_inst.data(), node_inst.size()) != cudaSuccess ||
+        cudaMalloc(&b->d_elem_buf, std::max<size_t>(1, (size_t)E * 12 * rs)) != cudaSuccess ||
+        cudaMalloc(&b->d_bend_buf, std::max<size_t>(1, (size_t)N * 6 * rs)) != cudaSuccess) {
+        ifem_batch_destroy(b);
+        return fail(ctx, IFEM_ERR_OOM, "batch: device allocation failed");
+    }
+    *out = b;
+    return IFEM_OK;
+}
+
+static void ws_free(Workspace &ws)
+{
+    for (void *p : ws.allocs)
+        cudaFree(p);
+    ws.allocs.clear();
+    ws.grid = nullptr;
+    ws.tile = 0;
+}
+
+extern "C" int ifem_batch_destroy(ifem_batch b)
+{
+    if (!b)
+        return IFEM_ERR_ARG;
+    ws_free(b->ws);
+    cudaFree(b->d_inst);
+    cudaFree(b->d_tmpl);
+    cudaFree(b->d_node_inst);
+    cudaFree(b->d_elem_buf);
+    cudaFree(b->d_bend_buf);
+    delete b;
+    return IFEM_OK;
+}
+
+extern "C" int64_t ifem_batch_nodes(ifem_batch b) { return b ? b->N : -1; }
+extern "C" int ifem_batch_instances(ifem_batch b) { return b ? (int)b->inst.size() : -1; }
+
+extern "C" int ifem_batch_set_origins(ifem_batch b, const double *origins)
+{
+    if (!b || !origins)
+        return IFEM_ERR_ARG;
+    ifem_ctx ctx = b->ctx;
+    for (size_t i = 0; i < b->h_inst.size(); ++i)
+        for (int a = 0; a < 3; ++a) {
+            if (!std::isfinite(origins[3 * i + a]))
+                return fail(ctx, IFEM_ERR_ARG, "set_origins: non-finite origin");
+            b->h_inst[i].origin[a] = origins[3 * i + a];
+        }
+    split_origins(b, b->grid0);
+    CK(cudaSetDevice(ctx->cfg.device));
+    if (!b->h_inst.empty())
+        CK(cudaMemcpy(b->d_inst, b->h_inst.data(), sizeof(InstDev) * b->h_inst.size(), cudaMemcpyHostToDevice));
+    return IFEM_OK;
+}
+
+static DevBatch dev_batch(ifem_batch b)
+{
+    DevBatch d{};
+    d.n_inst = (int)b->inst.size();
+    d.n_tmpl = (int)b->tmpls.size();
+    d.N = b->N;
+    d.max_nodes = b->max_nodes;
+    d.max_elems = b->max_elems;
+    d.n_elems_total = b->n_elems;
+    d.any_bending = b->any_bending;
+    d.fused_ok = b->fused_ok;
+    d.inst = b->d_inst;
+    d.tmpl = b->d_tmpl;
+    d.node_inst = b->d_node_inst;
+    return d;
+}
+
+// Work buffers for (batch, grid, tile): box/tile tables, per-tile lists.
+static int ws_ensure(ifem_ctx ctx, ifem_batch b, ifem_grid g, int tile)
+{
+    Workspace &ws = b->ws;
+    if (ws.grid == g && ws.tile == tile)
+        return IFEM_OK;
+    ws_free(ws);
+    std::vector<BoxDev> boxes(g->n_boxes);
+    long long nt = 0;
+    int max_edge = 0;
+    for (int i = 0; i < g->n_boxes; ++i) {
+        BoxDev &B = boxes[i];
+        B.n = g->n[i];
+        B.t = std::min(tile, B.n);
+        B.T = tiles_per_axis(B.n, B.t);
+        B.tile_base = nt;
+        B.grid_off = g->off[i];
+        B.L = g->L[i];
+        B.inv_h = (double)B.n / B.L;
+        B.scale = B.inv_h * B.inv_h * B.inv_h;
+        nt += (long long)B.T * B.T * B.T;
+        for (int j = 0; j < B.T; ++j)
+            max_edge = std::max(max_edge, tile_edge(j, B.t, B.T, B.n));
+    }
+    if (max_edge > kMaxTileEdge * 2)
+        return fail(ctx, IFEM_ERR_CAPACITY, "tile edge too large");
+    if (nt >= (1LL << 31) - 1)
+        return fail(ctx, IFEM_ERR_CAPACITY, "too many tiles");
+    auto alloc = [&](void **p, size_t bytes) -> cudaError_t {
+        cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+        if (e == cudaSuccess)
+            ws.allocs.push_back(*p);
+        return e;
+    };
+    DevWork &w = ws.w;
+    w = DevWork{};
+    long long N = b->N;
+    int nb = (int)((nt + kScanBlock - 1) / kScanBlock);
+    w.cand_cap = 8 * N;
+    CK(alloc((void **)&ws.d_boxes, sizeof(BoxDev) * boxes.size()));
+    CK(cudaMemcpy(ws.d_boxes, boxes.data(), sizeof(BoxDev) * boxes.size(), cudaMemcpyHostToDevice));
+    CK(alloc((void **)&w.cand_count, sizeof(int) * (nt + 1)));
+    CK(alloc((void **)&w.cand_off, sizeof(int) * (nt + 1)));
+    CK(alloc((void **)&w.cand_cursor, sizeof(int) * (nt + 1)));
+    CK(alloc((void **)&w.cand_nodes, sizeof(int) * (size_t)w.cand_cap));
+    CK(alloc((void **)&w.own_count, sizeof(int) * (nt + 1)));
+    CK(alloc((void **)&w.own_off, sizeof(int) * (nt + 1)));
+    CK(alloc((void **)&w.own_cursor, sizeof(int) * (nt + 1)));
+    CK(alloc((void **)&w.own_nodes, sizeof(int) * (size_t)std::max<long long>(N, 1)));
+    CK(alloc((void **)&w.active, sizeof(int) * (nt + 1)));
+    CK(alloc((void **)&w.own_active, sizeof(int) * (nt + 1)));
+    CK(alloc((void **)&w.counters, sizeof(int) * 8));
+    CK(alloc((void **)&w.scan_blocks, sizeof(int) * 2 * (nb + 1)));
+    CK(alloc((void **)&w.red_tile, sizeof(double) * 3 * (nt + 1)));
+    CK(cudaMemset(w.red_tile, 0, sizeof(double) * 3 * (nt + 1)));
+    w.elem_buf = b->d_elem_buf;
+    w.bend_buf = b->d_bend_buf;
+    w.status = ctx->d_status;
+    ws.grid = g;
+    ws.tile = tile;
+    ws.n_tiles = nt;
+    ws.max_edge = max_edge;
+    return IFEM_OK;
+}
+
+static DevGrid dev_grid(ifem_batch b)
+{
+    DevGrid d{};
+    d.n_boxes = b->ws.grid->n_boxes;
+    d.n_tiles = b->ws.n_tiles;
+    d.max_edge = b->ws.max_edge;
+    d.boxes = b->ws.d_boxes;
+    return d;
+}
+
+static int check_call(ifem_ctx ctx, ifem_batch b, ifem_grid g)
+{
+    if (!ctx || !b || b->ctx != ctx)
+        return fail(ctx, IFEM_ERR_ARG, "null or foreign batch");
+    if (g && (g->ctx != ctx || b->max_box >= g->n_boxes))
+        return fail(ctx, IFEM_ERR_ARG, "grid does not match the batch");
+    if (cudaSetDevice(ctx->cfg.device) != cudaSuccess)
+        return fail(ctx, IFEM_ERR_CUDA, "cudaSetDevice failed");
+    return IFEM_OK;
+}
+
+static int launch_rc(ifem_ctx ctx, cudaError_t e, const char *what)
+{
+    if (e != cudaSuccess)
+        return fail(ctx, IFEM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return IFEM_OK;
+}
+
+static TransferArgs transfer_args(ifem_ctx ctx, ifem_batch b, const void *x, const void *F, const void *u,
+                                  void *f, void *v, int flags, void *stream)
+{
+    TransferArgs a{};
+    a.b = dev_batch(b);
+    a.g = dev_grid(b);
+    a.w = b->ws.w;
+    a.x = x;
+    a.F = F;
+    a.u = u;
+    a.f = f;
+    a.v = v;
+    a.kernel = ctx->cfg.kernel;
+    a.density = (flags & IFEM_SPREAD_FORCE) ? 0 : 1;
+    a.support = ctx->cfg.mls_support;
+    a.n_sm = ctx->n_sm;
+    a.stream = (cudaStream_t)stream;
+    return a;
+}
+
+static int do_forces(ifem_ctx ctx, ifem_batch b, const void *x, void *F, const void *wv, int hvp, void *stream)
+{
+    ForcesArgs a{};
+    a.b = dev_batch(b);
+    a.w.elem_buf = b->d_elem_buf;
+    a.w.bend_buf = b->d_bend_buf;
+    a.w.status = ctx->d_status;
+    a.x = x;
+    a.F = F;
+    a.wv = wv;
+    a.scatter = ctx->cfg.scatter;
+    a.hvp = hvp;
+    a.stream = (cudaStream_t)stream;
+    cudaError_t e = ctx->cfg.precision == IFEM_FP64 ? launch_forces_f64(a) : launch_forces_f32(a);
+    return launch_rc(ctx, e, "forces");
+}
+
+static int do_bin(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, void *stream)
+{
+    int rc = ws_ensure(ctx, b, g, ctx->tile);
+    if (rc != IFEM_OK)
+        return rc;
+    TransferArgs a = transfer_args(ctx, b, x, nullptr, nullptr, nullptr, nullptr, 0, stream);
+    cudaError_t e = ctx->cfg.precision == IFEM_FP64 ? launch_bin_f64(a, 1) : launch_bin_f32(a, 0);
+    return launch_rc(ctx, e, "binning");
+}
+
+static int do_spread(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *F, void *f, int flags,
+                     void *stream)
+{
+    if (flags & IFEM_SPREAD_OVERWRITE) {
+        cudaError_t e = cudaMemsetAsync(f, 0, (size_t)g->total * real_size(ctx), (cudaStream_t)stream);
+        if (e != cudaSuccess)
+            return launch_rc(ctx, e, "spread overwrite");
+    }
+    TransferArgs a = transfer_args(ctx, b, x, F, nullptr, f, nullptr, flags, stream);
+    cudaError_t e = ctx->cfg.precision == IFEM_FP64 ? launch_spread_f64(a) : launch_spread_f32(a);
+    return launch_rc(ctx, e, "spread");
+}
+
+static int do_interp(ifem_ctx ctx, ifem_batch b, const void *u, const void *x, void *v, void *stream)
+{
+    TransferArgs a = transfer_args(ctx, b, x, nullptr, u, nullptr, v, 0, stream);
+    cudaError_t e = ctx->cfg.precision == IFEM_FP64 ? launch_interp_f64(a) : launch_interp_f32(a);
+    return launch_rc(ctx, e, "interpolate");
+}
+
+static int do_reduce(ifem_ctx ctx, ifem_batch b, const void *x, const void *F, const void *v, double *red,
+                     void *stream)
+{
+    ReduceArgs a{};
+    a.b = dev_batch(b);
+    a.g = dev_grid(b);
+    a.w = b->ws.w;
+    a.x = x;
+    a.F = F;
+    a.v = v;
+    a.red = red;
+    a.stream = (cudaStream_t)stream;
+    cudaError_t e = ctx->cfg.precision == IFEM_FP64 ? launch_reduce_f64(a) : launch_reduce_f32(a);
+    return launch_rc(ctx, e, "reduce");
+}
+
+// ------------------------------------------------------------ compute
+extern "C" int ifem_compute_forces(ifem_ctx ctx, ifem_batch b, const void *x, void *F, void *stream)
+{
+    int rc = check_call(ctx, b, nullptr);
+    if (rc != IFEM_OK)
+        return rc;
+    if ((!x || !F) && b->N > 0)
+        return fail(ctx, IFEM_ERR_ARG, "compute_forces: null array");
+    return do_forces(ctx, b, x, F, nullptr, 0, stream);
+}
+
+extern "C" int ifem_force_hvp(ifem_ctx ctx, ifem_batch b, const void *x, const void *w, void *Hw, void *stream)
+{
+    int rc = check_call(ctx, b, nullptr);
+    if (rc != IFEM_OK)
+        return rc;
+    if ((!x || !w || !Hw) && b->N > 0)
+        return fail(ctx, IFEM_ERR_ARG, "force_hvp: null array");
+    return do_forces(ctx, b, x, Hw, w, 1, stream);
+}
+
+extern "C" int ifem_spread(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *F, void *f,
+                           int flags, void *stream)
+{
+    int rc = check_call(ctx, b, g);
+    if (rc != IFEM_OK)
+        return rc;
+    if (!g || !f || ((!x || !F) && b->N > 0))
+        return fail(ctx, IFEM_ERR_ARG, "spread: null array or grid");
+    if (flags & ~(IFEM_SPREAD_FORCE | IFEM_SPREAD_OVERWRITE))
+        return fail(ctx, IFEM_ERR_ARG, "spread: unknown flags");
+    if ((rc = do_bin(ctx, b, g, x, stream)) != IFEM_OK)
+        return rc;
+    return do_spread(ctx, b, g, x, F, f, flags, stream);
+}
+
+extern "C" int ifem_interpolate(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *u, const void *x, void *v,
+                                void *stream)
+{
+    int rc = check_call(ctx, b, g);
+    if (rc != IFEM_OK)
+        return rc;
+    if (!g || !u || ((!x || !v) && b->N > 0))
+        return fail(ctx, IFEM_ERR_ARG, "interpolate: null array or grid");
+    if (ctx->cfg.precision == IFEM_FP32) {
+        // the FP32 kernel walks the nodes in tile order (locality)
+        if ((rc = do_bin(ctx, b, g, x, stream)) != IFEM_OK)
+            return rc;
+    } else if ((rc = ws_ensure(ctx, b, g, ctx->tile)) != IFEM_OK) {
+        return rc;
+    }
+    return do_interp(ctx, b, u, x, v, stream);
+}
+
+extern "C" int ifem_reduce(ifem_ctx ctx, ifem_batch b, const void *x, const void *F, const void *v, double *red,
+                           void *stream)
+{
+    int rc = check_call(ctx, b, nullptr);
+    if (rc != IFEM_OK)
+        return rc;
+    if (!red || (!x && b->N > 0))
+        return fail(ctx, IFEM_ERR_ARG, "reduce: null array");
+    if ((rc = ws_ensure(ctx, b, b->grid0, ctx->tile)) != IFEM_OK)
+        return rc;
+    return do_reduce(ctx, b, x, F, v, red, stream);
+}
+
+extern "C" int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *u, void *F,
+                                  void *f, void *v, double *red, int flags, void *stream)
+{
+    int rc = check_call(ctx, b, g);
+    if (rc != IFEM_OK)
+        return rc;
+    if (!g || !u || !f || ((!x || !F || !v) && b->N > 0))
+        return fail(ctx, IFEM_ERR_ARG, "step_coupling: null array or grid");
+    if (flags & ~(IFEM_SPREAD_FORCE | IFEM_SPREAD_OVERWRITE))
+        return fail(ctx, IFEM_ERR_ARG, "step_coupling: unknown flags");
+    mark(ctx, 0, stream);
+    if ((rc = do_bin(ctx, b, g, x, stream)) != IFEM_OK)
+        return rc;
+    mark(ctx, 1, stream);
+    if ((rc = do_forces(ctx, b, x, F, nullptr, 0, stream)) != IFEM_OK)
+        return rc;
+    mark(ctx, 2, stream);
+    if ((rc = do_spread(ctx, b, g, x, F, f, flags, stream)) != IFEM_OK)
+        return rc;
+    mark(ctx, 3, stream);
+    if ((rc = do_interp(ctx, b, u, x, v, stream)) != IFEM_OK)
+        return rc;
+    mark(ctx, 4, stream);
+    if (red && (rc = do_reduce(ctx, b, x, F, v, red, stream)) != IFEM_OK)
+        return rc;
+    mark(ctx, 5, stream);
+    ctx->ev_recorded = ctx->ev_ok;
+    return IFEM_OK;
+}
+
+extern "C" int ifem_prepare(ifem_ctx ctx, ifem_batch b, const void *x, void *stream)
+{
+    int rc = check_call(ctx, b, nullptr);
+    if (rc != IFEM_OK)
+        return rc;
+    (void)x;
+    (void)stream;
+    return ws_ensure(ctx, b, b->grid0, ctx->tile);
+}

@@ -1,0 +1,13 @@
+// kernels_f64.cu -- FP64 deterministic instantiation of the libifem kernels.
+// Compiled with --fmad=false: every multiply and add rounds separately, in
+// the evaluation order written in the kernels, so results are bit-identical
+// to a plain IEEE FP64 evaluation of the same expressions.
+#include "launch_impl.cuh"
+
+namespace ifem {
+cudaError_t launch_forces_f64(const ForcesArgs &a) { return forces_impl<double>(a); }
+cudaError_t launch_bin_f64(const TransferArgs &a, int det_sort) { return bin_impl<double>(a, det_sort); }
+cudaError_t launch_spread_f64(const TransferArgs &a) { return spread_impl<double>(a); }
+cudaError_t launch_interp_f64(const TransferArgs &a) { return interp_impl<double>(a); }
+cudaError_t launch_reduce_f64(const ReduceArgs &a) { return reduce_impl<double>(a); }
+}  // namespace ifem

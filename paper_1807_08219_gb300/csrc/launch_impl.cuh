@@ -1,0 +1,154 @@
+// launch_impl.cuh -- host-side launch sequences, instantiated once per
+// precision (kernels_f32.cu with FMA contraction, kernels_f64.cu without).
+#pragma once
+#include <type_traits>
+
+#include "common.cuh"
+#include "forces.cuh"
+#include "transfer.cuh"
+
+namespace ifem {
+
+#define IFEM_LAUNCH_CHECK()                      \
+    do {                                         \
+        cudaError_t e_ = cudaGetLastError();     \
+        if (e_ != cudaSuccess)                   \
+            return e_;                           \
+    } while (0)
+
+template <typename real>
+cudaError_t forces_impl(const ForcesArgs &a)
+{
+    const DevBatch &b = a.b;
+    if (b.n_inst == 0)
+        return cudaSuccess;
+    const real *x = (const real *)a.x;
+    real *F = (real *)a.F;
+    cudaStream_t s = a.stream;
+    if constexpr (std::is_same<real, float>::value) {
+        if (!a.hvp && a.scatter == 1 && b.fused_ok) {
+        size_t sm = fused_smem_bytes(b.max_nodes);
+        cudaFuncSetAttribute(forces_fused_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        forces_fused_f32_kernel<<<b.n_inst, 512, sm, s>>>(b, (const float *)a.x, (float *)a.F, a.w.status);
+        IFEM_LAUNCH_CHECK();
+        return cudaSuccess;
+        }
+    }
+    dim3 blk(256);
+    dim3 ge((b.max_elems + 255) / 256, b.n_inst);
+    dim3 gn((b.max_nodes + 255) / 256, b.n_inst);
+    real *ebuf = (real *)a.w.elem_buf;
+    if (a.hvp)
+        elem_force_kernel<real, true><<<ge, blk, 0, s>>>(b, x, (const real *)a.wv, ebuf, a.w.status);
+    else
+        elem_force_kernel<real, false><<<ge, blk, 0, s>>>(b, x, nullptr, ebuf, a.w.status);
+    IFEM_LAUNCH_CHECK();
+    node_gather_kernel<real><<<gn, blk, 0, s>>>(b, ebuf, F);
+    IFEM_LAUNCH_CHECK();
+    if (!a.hvp && b.any_bending) {
+        real *bb = (real *)a.w.bend_buf;
+        bend_pass1_kernel<real><<<gn, blk, 0, s>>>(b, x, bb);
+        IFEM_LAUNCH_CHECK();
+        bend_pass2_kernel<real><<<gn, blk, 0, s>>>(b, x, bb, F);
+        IFEM_LAUNCH_CHECK();
+    }
+    return cudaSuccess;
+}
+
+template <typename real>
+cudaError_t bin_impl(const TransferArgs &a, int det_sort)
+{
+    const DevBatch &b = a.b;
+    const DevWork &w = a.w;
+    const long long nt = a.g.n_tiles;
+    cudaStream_t s = a.stream;
+    cudaMemsetAsync(w.cand_count, 0, sizeof(int) * (nt + 1), s);
+    cudaMemsetAsync(w.own_count, 0, sizeof(int) * (nt + 1), s);
+    cudaMemsetAsync(w.counters, 0, sizeof(int) * 8, s);
+    IFEM_LAUNCH_CHECK();
+    if (b.n_inst == 0 || b.N == 0)
+        return cudaSuccess;
+    dim3 gn((b.max_nodes + 255) / 256, b.n_inst);
+    bin_kernel<real, false><<<gn, 256, 0, s>>>(b, a.g, w, (const real *)a.x);
+    IFEM_LAUNCH_CHECK();
+    int nb = (int)((nt + kScanBlock - 1) / kScanBlock);
+    scan_local_kernel<<<nb, kScanThreads, 0, s>>>(nt, w.cand_count, w.own_count, w.cand_off, w.own_off,
+                                                  w.scan_blocks);
+    IFEM_LAUNCH_CHECK();
+    scan_blocks_kernel<<<1, 1024, 0, s>>>(nb, w.scan_blocks, w.counters + 4);
+    IFEM_LAUNCH_CHECK();
+    scan_finish_kernel<<<(unsigned)((nt + 1 + 255) / 256), 256, 0, s>>>(nt, w);
+    IFEM_LAUNCH_CHECK();
+    bin_kernel<real, true><<<gn, 256, 0, s>>>(b, a.g, w, (const real *)a.x);
+    IFEM_LAUNCH_CHECK();
+    if (det_sort) {
+        sort_segments_kernel<<<a.n_sm * 4, 512, 0, s>>>(w);
+        IFEM_LAUNCH_CHECK();
+    }
+    return cudaSuccess;
+}
+
+template <typename real>
+cudaError_t spread_impl(const TransferArgs &a)
+{
+    const DevBatch &b = a.b;
+    cudaStream_t s = a.stream;
+    cudaMemsetAsync(a.w.red_tile, 0, sizeof(double) * 3 * a.g.n_tiles, s);
+    IFEM_LAUNCH_CHECK();
+    if (b.n_inst == 0 || b.N == 0)
+        return cudaSuccess;
+    if constexpr (std::is_same<real, float>::value) {
+        const int E = a.g.max_edge;
+        size_t sm = sizeof(float) * 3 * (size_t)E * E * E;
+        auto kern = a.kernel == 0 ? spread_fast_kernel<0> : spread_fast_kernel<1>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        int occ = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, sm);
+        occ = occ < 1 ? 1 : occ;
+        kern<<<a.n_sm * occ, 256, sm, s>>>(b, a.g, a.w, (const float *)a.x, (const float *)a.F, (float *)a.f,
+                                           a.density, (float)a.support);
+    } else {
+        auto kern = a.kernel == 0 ? spread_det_kernel<0> : spread_det_kernel<1>;
+        int occ = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kDetThreads, 0);
+        occ = occ < 1 ? 1 : occ;
+        kern<<<a.n_sm * occ, kDetThreads, 0, s>>>(b, a.g, a.w, (const double *)a.x, (const double *)a.F,
+                                                  (double *)a.f, a.density, a.support);
+    }
+    IFEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
+template <typename real>
+cudaError_t interp_impl(const TransferArgs &a)
+{
+    const DevBatch &b = a.b;
+    if (b.n_inst == 0 || b.N == 0)
+        return cudaSuccess;
+    constexpr bool DET = std::is_same<real, double>::value;
+    unsigned grid = (unsigned)((b.N + 255) / 256);
+    int use_order = DET ? 0 : 1;
+    if (a.kernel == 0)
+        interp_kernel<real, DET, 0><<<grid, 256, 0, a.stream>>>(b, a.g, a.w, (const real *)a.u, (const real *)a.x,
+                                                              (real *)a.v, (real)a.support, use_order);
+    else
+        interp_kernel<real, DET, 1><<<grid, 256, 0, a.stream>>>(b, a.g, a.w, (const real *)a.u, (const real *)a.x,
+                                                              (real *)a.v, (real)a.support, use_order);
+    IFEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
+template <typename real>
+cudaError_t reduce_impl(const ReduceArgs &a)
+{
+    if (a.b.n_inst > 0) {
+        reduce_inst_kernel<real><<<a.b.n_inst, 256, 0, a.stream>>>(a.b, (const real *)a.x, (const real *)a.F,
+                                                                   (const real *)a.v, a.red);
+        IFEM_LAUNCH_CHECK();
+    }
+    reduce_box_kernel<<<a.g.n_boxes, 256, 0, a.stream>>>(a.g, a.w.red_tile, a.red + 12LL * a.b.n_inst);
+    IFEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
+}  // namespace ifem

@@ -1,0 +1,830 @@
+// transfer.cuh -- node binning, spreading S* and interpolation S
+// (Sec. "Interpolation Scheme"; Algorithm steps 2 and 4), and the FP64
+// conservation sums.
+//
+// Binning. Every node is assigned the cell c = floor(x n/L) of its box. For
+// both kernels and all three MAC lattices its stencil lies inside cells
+// c-2 .. c+2 per axis. Boxes are cut into tiles (edge t, the last tile per
+// axis t..t+4 cells, never fewer than 5), so the stencil meets at most two
+// tiles per axis. The binning writes
+//   cand lists: for every tile, the nodes whose stencil meets it (spread);
+//   own lists:  for every tile, the nodes whose cell lies in it (interp).
+// Spreading is owner-computes: the CTA that owns a tile accumulates every
+// contribution that lands in it and writes each touched value once, so no
+// global atomics are needed and no value is written by two CTAs.
+#pragma once
+#include "common.cuh"
+
+namespace ifem {
+
+struct TileInfo {
+    int box;
+    int start[3];
+    int edge[3];
+};
+
+__device__ inline int box_of_tile(const DevGrid &g, long long tile)
+{
+    int lo = 0, hi = g.n_boxes - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (g.boxes[mid].tile_base <= tile)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ inline TileInfo decode_tile(const DevGrid &g, long long tile)
+{
+    TileInfo ti;
+    ti.box = box_of_tile(g, tile);
+    const BoxDev &B = g.boxes[ti.box];
+    long long local = tile - B.tile_base;
+    int j[3] = {(int)(local % B.T), (int)((local / B.T) % B.T), (int)(local / ((long long)B.T * B.T))};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        ti.start[a] = tile_start(j[a], B.t);
+        ti.edge[a] = tile_edge(j[a], B.t, B.T, B.n);
+    }
+    return ti;
+}
+
+__device__ __forceinline__ float mac_off(int d, int a) { return a == d ? 0.f : 0.5f; }
+
+// ---------------------------------------------------------------- binning
+template <typename real>
+__device__ inline bool node_cell(const InstDev &I, const BoxDev &B, const real *x, long long N, int node,
+                                 int c[3])
+{
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        real xa = x[a * N + node];
+        ok = ok && isfinite(xa);
+        int I0;
+        real s = LatCoord<real>::get(I, B, a, xa, real(0), I0);
+        c[a] = ok ? wrapi((long long)I0 + (long long)floor(s), B.n) : 0;
+    }
+    return ok;
+}
+
+// FILL = false: count candidate / own pairs per tile; FILL = true: write them.
+template <typename real, bool FILL>
+__global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restrict__ x)
+{
+    const InstDev I = b.inst[blockIdx.y];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= I.n_nodes)
+        return;
+    const BoxDev B = g.boxes[I.box];
+    const int node = I.node_off + k;
+    int c[3];
+    if (!node_cell<real>(I, B, x, b.N, node, c)) {
+        if (!FILL)
+            status_add(w.status, ST_DOMAIN, 1);
+        return;
+    }
+    int tl[3][2], nt[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        tl[a][0] = tile_of(wrapi(c[a] - 2, B.n), B.t, B.T);
+        tl[a][1] = tile_of(wrapi(c[a] + 2, B.n), B.t, B.T);
+        nt[a] = tl[a][0] == tl[a][1] ? 1 : 2;
+    }
+    long long own = B.tile_base + ((long long)tile_of(c[2], B.t, B.T) * B.T + tile_of(c[1], B.t, B.T)) * B.T
+                    + tile_of(c[0], B.t, B.T);
+    if (FILL) {
+        int p = atomicAdd(&w.own_cursor[own], 1);
+        w.own_nodes[p] = node;
+    } else {
+        atomicAdd(&w.own_count[own], 1);
+    }
+    for (int iz = 0; iz < nt[2]; ++iz)
+        for (int iy = 0; iy < nt[1]; ++iy)
+            for (int ix = 0; ix < nt[0]; ++ix) {
+                long long tile = B.tile_base + ((long long)tl[2][iz] * B.T + tl[1][iy]) * B.T + tl[0][ix];
+                if (FILL) {
+                    int p = atomicAdd(&w.cand_cursor[tile], 1);
+                    w.cand_nodes[p] = node;
+                } else {
+                    atomicAdd(&w.cand_count[tile], 1);
+                }
+            }
+}
+
+// Exclusive scan of the per-tile counts (two lists at once), 3 passes:
+// block-local scan -> scan of block sums -> add + cursors + active lists.
+
+__device__ inline int block_exclusive_scan(int v, int *sh, int &total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o)
+            incl += t;
+    }
+    if (lane == 31)
+        sh[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int s = lane < nw ? sh[lane] : 0;
+        int si = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o)
+                si += t;
+        }
+        if (lane < nw)
+            sh[lane] = si - s;
+        if (lane == nw - 1)
+            sh[32] = si;
+    }
+    __syncthreads();
+    int r = sh[wid] + incl - v;
+    total = sh[32];
+    __syncthreads();
+    return r;
+}
+
+static __global__ void scan_local_kernel(long long n, const int *__restrict__ c1, const int *__restrict__ c2,
+                                  int *__restrict__ o1, int *__restrict__ o2, int *__restrict__ bsum)
+{
+    __shared__ int sh[33];
+    long long base = (long long)blockIdx.x * kScanBlock + (long long)threadIdx.x * kScanPer;
+    int v1[kScanPer], v2[kScanPer], s1 = 0, s2 = 0;
+#pragma unroll
+    for (int q = 0; q < kScanPer; ++q) {
+        long long i = base + q;
+        v1[q] = i < n ? c1[i] : 0;
+        v2[q] = i < n ? c2[i] : 0;
+        s1 += v1[q];
+        s2 += v2[q];
+    }
+    int t1, t2;
+    int e1 = block_exclusive_scan(s1, sh, t1);
+    int e2 = block_exclusive_scan(s2, sh, t2);
+#pragma unroll
+    for (int q = 0; q < kScanPer; ++q) {
+        long long i = base + q;
+        if (i < n) {
+            o1[i] = e1;
+            o2[i] = e2;
+        }
+        e1 += v1[q];
+        e2 += v2[q];
+    }
+    if (threadIdx.x == 0) {
+        bsum[2 * blockIdx.x] = t1;
+        bsum[2 * blockIdx.x + 1] = t2;
+    }
+}
+
+static __global__ void scan_blocks_kernel(int nb, int *__restrict__ bsum, int *__restrict__ totals)
+{
+    __shared__ int sh[33];
+    int run1 = 0, run2 = 0;
+    for (int base = 0; base < nb; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        int v1 = i < nb ? bsum[2 * i] : 0, v2 = i < nb ? bsum[2 * i + 1] : 0;
+        int t1, t2;
+        int e1 = block_exclusive_scan(v1, sh, t1);
+        int e2 = block_exclusive_scan(v2, sh, t2);
+        if (i < nb) {
+            bsum[2 * i] = e1 + run1;
+            bsum[2 * i + 1] = e2 + run2;
+        }
+        run1 += t1;
+        run2 += t2;
+    }
+    if (threadIdx.x == 0) {
+        totals[0] = run1;
+        totals[1] = run2;
+    }
+}
+
+static __global__ void scan_finish_kernel(long long n, DevWork w)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n)
+        return;
+    int blk = (int)(i / kScanBlock);
+    if (i == n) {
+        // terminal offsets
+        w.cand_off[n] = w.counters[4];
+        w.own_off[n] = w.counters[5];
+        return;
+    }
+    int c1 = w.cand_count[i], c2 = w.own_count[i];
+    int o1 = w.cand_off[i] + w.scan_blocks[2 * blk];
+    int o2 = w.own_off[i] + w.scan_blocks[2 * blk + 1];
+    w.cand_off[i] = o1;
+    w.own_off[i] = o2;
+    w.cand_cursor[i] = o1;
+    w.own_cursor[i] = o2;
+    // active lists (order irrelevant: every tile is processed independently)
+    unsigned m1 = __ballot_sync(__activemask(), c1 > 0);
+    unsigned m2 = __ballot_sync(__activemask(), c2 > 0);
+    const int lane = threadIdx.x & 31;
+    int leader = __ffs(__activemask()) - 1;
+    int b1 = 0, b2 = 0;
+    if (lane == leader) {
+        if (m1)
+            b1 = atomicAdd(&w.counters[0], __popc(m1));
+        if (m2)
+            b2 = atomicAdd(&w.counters[1], __popc(m2));
+    }
+    b1 = __shfl_sync(__activemask(), b1, leader);
+    b2 = __shfl_sync(__activemask(), b2, leader);
+    unsigned below = (1u << lane) - 1u;
+    if (c1 > 0)
+        w.active[b1 + __popc(m1 & below)] = (int)i;
+    if (c2 > 0)
+        w.own_active[b2 + __popc(m2 & below)] = (int)i;
+}
+
+// Deterministic mode: sort each tile's candidate list by node id (bitonic
+// sort in shared memory). Lists longer than kSortCap are flagged.
+constexpr int kSortCap = 4096;
+static __global__ void sort_segments_kernel(DevWork w)
+{
+    __shared__ int key[kSortCap];
+    const int n_active = w.counters[0];
+    for (int it = blockIdx.x; it < n_active; it += gridDim.x) {
+        const int tile = w.active[it];
+        const int beg = w.cand_off[tile], len = w.cand_off[tile + 1] - beg;
+        if (len > kSortCap) {
+            if (threadIdx.x == 0)
+                status_add(w.status, ST_CAPACITY, 1);
+            continue;
+        }
+        int P = 1;
+        while (P < len)
+            P <<= 1;
+        for (int i = threadIdx.x; i < P; i += blockDim.x)
+            key[i] = i < len ? w.cand_nodes[beg + i] : 0x7fffffff;
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                    int l = i ^ j;
+                    if (l > i) {
+                        int a = key[i], bb = key[l];
+                        bool up = (i & k) == 0;
+                        if ((a > bb) == up) {
+                            key[i] = bb;
+                            key[l] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int i = threadIdx.x; i < len; i += blockDim.x)
+            w.cand_nodes[beg + i] = key[i];
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------------------- stencil per axis
+// Peskin: i0 = floor(s) - 1 (relative to I0), phi[m] = phi4(s - (i0 + m)).
+template <typename real>
+__device__ __forceinline__ long long peskin_axis(real s, real ph[4])
+{
+    long long i0 = (long long)floor(s) - 1;
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        ph[m] = phi4<real>(s - (real)(i0 + m));
+    return i0;
+}
+
+// ---------------------------------------------------- spread, FP32 fast
+// One CTA per active tile (grid-stride over the active list). Shared
+// memory: the tile's owned values of the three lattices, accumulated with
+// shared-memory atomics; flushed with one read-modify-write per non-zero
+// value. Per-tile FP64 sums of the added values go to red_tile[3*tile + d].
+template <int KER>
+__global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g, DevWork w,
+                                                          const float *__restrict__ x,
+                                                          const float *__restrict__ F, float *__restrict__ f,
+                                                          int density, float support)
+{
+    extern __shared__ float acc[];
+    __shared__ double red_sh[3][8];
+    const long long N = b.N;
+    const int n_active = w.counters[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        status_add(w.status, ST_PAIRS, (unsigned long long)w.cand_off[g.n_tiles]);
+        status_add(w.status, ST_ACTIVE, (unsigned long long)n_active);
+    }
+    for (int it = blockIdx.x; it < n_active; it += gridDim.x) {
+        const int tile = w.active[it];
+        const TileInfo ti = decode_tile(g, tile);
+        const BoxDev B = g.boxes[ti.box];
+        const int ex = ti.edge[0], ey = ti.edge[1], ez = ti.edge[2];
+        const int vol = ex * ey * ez;
+        for (int i = threadIdx.x; i < 3 * vol; i += blockDim.x)
+            acc[i] = 0.f;
+        __syncthreads();
+        const float scale = density ? (float)B.scale : 1.f;
+        const int beg = w.cand_off[tile], end = w.cand_off[tile + 1];
+        for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
+            const int node = w.cand_nodes[q];
+            const InstDev I = b.inst[b.node_inst[node]];
+            float xl[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                xl[a] = x[a * N + node];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float gd = F[d * N + node] * scale;
+                float* accd = acc + d * vol;
+                if constexpr (KER == 0) {
+                    float ph[3][4];
+                    int loc[3][4];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        int I0;
+                        float s = LatCoord<float>::get(I, B, a, xl[a], mac_off(d, a), I0);
+                        long long i0 = peskin_axis<float>(s, ph[a]);
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            int l = wrapi(I0 + i0 + m, B.n) - ti.start[a];
+                            loc[a][m] = (l >= 0 && l < ti.edge[a]) ? l : -1;
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        if (loc[2][c] < 0)
+                            continue;
+#pragma unroll
+                        for (int bb = 0; bb < 4; ++bb) {
+                            if (loc[1][bb] < 0)
+                                continue;
+                            const float wyz = ph[1][bb] * ph[2][c] * gd;
+                            const int row = (loc[2][c] * ey + loc[1][bb]) * ex;
+#pragma unroll
+                            for (int a = 0; a < 4; ++a)
+                                if (loc[0][a] >= 0)
+                                    atomicAdd(&accd[row + loc[0][a]], ph[0][a] * wyz);
+                        }
+                    }
+                } else {
+                    float s[3];
+                    int I0[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        s[a] = LatCoord<float>::get(I, B, a, xl[a], mac_off(d, a), I0[a]);
+                    int base[3];
+                    float wt[27];
+                    if (!mls_weights<float>(s, support, base, wt)) {
+                        status_add(w.status, ST_DOMAIN, 1);
+                        continue;
+                    }
+                    int loc[3][3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int m = 0; m < 3; ++m) {
+                            int l = wrapi((long long)I0[a] + base[a] + m, B.n) - ti.start[a];
+                            loc[a][m] = (l >= 0 && l < ti.edge[a]) ? l : -1;
+                        }
+                    int J = 0;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+#pragma unroll
+                        for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+                            for (int a = 0; a < 3; ++a, ++J)
+                                if (loc[2][c] >= 0 && loc[1][bb] >= 0 && loc[0][a] >= 0)
+                                    atomicAdd(&accd[(loc[2][c] * ey + loc[1][bb]) * ex + loc[0][a]], wt[J] * gd);
+                }
+            }
+        }
+        __syncthreads();
+        // flush: f += acc for every non-zero owned value; FP64 tile sums
+        const long long n3 = (long long)B.n * B.n * B.n;
+        double part[3] = {0.0, 0.0, 0.0};
+        unsigned long long touched = 0;
+        for (int d = 0; d < 3; ++d) {
+            float *fd = f + B.grid_off + d * n3;
+            for (int i = threadIdx.x; i < vol; i += blockDim.x) {
+                float v = acc[d * vol + i];
+                if (v != 0.f) {
+                    int lx = i % ex, ly = (i / ex) % ey, lz = i / (ex * ey);
+                    long long gi = ((long long)(ti.start[2] + lz) * B.n + (ti.start[1] + ly)) * B.n
+                                   + (ti.start[0] + lx);
+                    fd[gi] += v;
+                    part[d] += (double)v;
+                    ++touched;
+                }
+            }
+        }
+        // fixed-order block reduction of part[]; count of touched values
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        {
+            unsigned long long cnt = touched;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+            if (lane == 0)
+                status_add(w.status, ST_TOUCHED, cnt);
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double v = part[d];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0)
+                red_sh[d][wid] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            double v = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
+                v += red_sh[threadIdx.x][q];
+            w.red_tile[3LL * tile + threadIdx.x] = v * (1.0 / B.scale);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------- spread, FP64 deterministic
+// Owner-computes gather: each thread owns up to kDetCells values of the tile
+// (per lattice), starts from the current grid value and adds the
+// contributions of the tile's candidate nodes in ascending node order:
+// f = f + w*g, w = (phi_x*phi_y)*phi_z, g = F*scale. This is the oracle's
+// per-value summation order, so the result is bit-identical.
+constexpr int kDetThreads = 256;
+constexpr int kDetCells = 8;     // owned values per thread and lattice: vol <= 2048
+constexpr int kDetChunk = 32;    // candidates staged per round
+
+template <int KER>
+struct DetCand;
+template <>
+struct DetCand<0> {
+    int lo[3];            // wrapped cell c-2 (union reach of all lattices)
+    int base[3][3];       // [d][a] wrapped i0
+    double ph[3][3][4];   // [d][a][m]
+    double g[3];
+    int ok;
+};
+template <>
+struct DetCand<1> {
+    int lo[3];
+    int base[3][3];
+    double wt[3][27];
+    double g[3];
+    int ok;
+};
+
+template <int KER>
+__global__ void __launch_bounds__(kDetThreads) spread_det_kernel(DevBatch b, DevGrid g, DevWork w,
+                                                                 const double *__restrict__ x,
+                                                                 const double *__restrict__ F,
+                                                                 double *__restrict__ f, int density,
+                                                                 double support)
+{
+    __shared__ DetCand<KER> cand[kDetChunk];
+    __shared__ double red_sh[3][kDetThreads / 32];
+    const long long N = b.N;
+    const int n_active = w.counters[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        status_add(w.status, ST_PAIRS, (unsigned long long)w.cand_off[g.n_tiles]);
+        status_add(w.status, ST_ACTIVE, (unsigned long long)n_active);
+    }
+    for (int it = blockIdx.x; it < n_active; it += gridDim.x) {
+        const int tile = w.active[it];
+        const TileInfo ti = decode_tile(g, tile);
+        const BoxDev B = g.boxes[ti.box];
+        const int ex = ti.edge[0], ey = ti.edge[1], ez = ti.edge[2];
+        const int vol = ex * ey * ez;
+        const long long n3 = (long long)B.n * B.n * B.n;
+        if (vol > kDetThreads * kDetCells) {
+            if (threadIdx.x == 0)
+                status_add(w.status, ST_CAPACITY, 1);
+            continue;
+        }
+        double accv[kDetCells][3], init[kDetCells][3];
+        int cx[kDetCells], cy[kDetCells], cz[kDetCells];
+#pragma unroll
+        for (int q = 0; q < kDetCells; ++q) {
+            int i = threadIdx.x + q * kDetThreads;
+            int lx = i % ex, ly = (i / ex) % ey, lz = i / (ex * ey);
+            cx[q] = ti.start[0] + lx;
+            cy[q] = ti.start[1] + ly;
+            cz[q] = ti.start[2] + lz;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                double v = 0.0;
+                if (i < vol)
+                    v = f[B.grid_off + d * n3 + ((long long)cz[q] * B.n + cy[q]) * B.n + cx[q]];
+                accv[q][d] = v;
+                init[q][d] = v;
+            }
+        }
+        const double scale = density ? B.scale : 1.0;
+        const int beg = w.cand_off[tile], end = w.cand_off[tile + 1];
+        for (int c0 = beg; c0 < end; c0 += kDetChunk) {
+            const int nc = min(kDetChunk, end - c0);
+            __syncthreads();
+            // stage candidate data: one thread per (candidate, lattice)
+            for (int t = threadIdx.x; t < nc * 3; t += blockDim.x) {
+                const int j = t / 3, d = t % 3;
+                const int node = w.cand_nodes[c0 + j];
+                const InstDev I = b.inst[b.node_inst[node]];
+                DetCand<KER> &C = cand[j];
+                double s[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    int I0;
+                    s[a] = LatCoord<double>::get(I, B, a, x[a * N + node], (double)mac_off(d, a), I0);
+                }
+                if (d == 0) {
+                    C.ok = 1;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        int I0;
+                        double sc = LatCoord<double>::get(I, B, a, x[a * N + node], 0.0, I0);
+                        C.lo[a] = wrapi((long long)floor(sc) - 2, B.n);
+                    }
+                }
+                C.g[d] = F[d * N + node] * scale;
+                if constexpr (KER == 0) {
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        C.base[d][a] = wrapi(peskin_axis<double>(s[a], C.ph[d][a]), B.n);
+                } else {
+                    int base[3];
+                    if (!mls_weights<double>(s, support, base, C.wt[d])) {
+                        status_add(w.status, ST_DOMAIN, 1);
+                        C.g[d] = 0.0;
+#pragma unroll
+                        for (int J = 0; J < 27; ++J)
+                            C.wt[d][J] = 0.0;
+                    }
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        C.base[d][a] = wrapi(base[a], B.n);
+                }
+            }
+            __syncthreads();
+            for (int j = 0; j < nc; ++j) {
+                const DetCand<KER> &C = cand[j];
+#pragma unroll
+                for (int q = 0; q < kDetCells; ++q) {
+                    if (threadIdx.x + q * kDetThreads >= vol)
+                        break;
+                    int rx = cx[q] - C.lo[0], ry = cy[q] - C.lo[1], rz = cz[q] - C.lo[2];
+                    rx += rx < 0 ? B.n : 0;
+                    ry += ry < 0 ? B.n : 0;
+                    rz += rz < 0 ? B.n : 0;
+                    if (rx > 4 || ry > 4 || rz > 4)
+                        continue;
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        int mx = cx[q] - C.base[d][0], my = cy[q] - C.base[d][1], mz = cz[q] - C.base[d][2];
+                        mx += mx < 0 ? B.n : 0;
+                        my += my < 0 ? B.n : 0;
+                        mz += mz < 0 ? B.n : 0;
+                        if constexpr (KER == 0) {
+                            if (mx <= 3 && my <= 3 && mz <= 3) {
+                                double wgt = (C.ph[d][0][mx] * C.ph[d][1][my]) * C.ph[d][2][mz];
+                                accv[q][d] = accv[q][d] + wgt * C.g[d];
+                            }
+                        } else {
+                            if (mx <= 2 && my <= 2 && mz <= 2)
+                                accv[q][d] = accv[q][d] + C.wt[d][(mz * 3 + my) * 3 + mx] * C.g[d];
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        double part[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int q = 0; q < kDetCells; ++q) {
+            int i = threadIdx.x + q * kDetThreads;
+            if (i >= vol)
+                break;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                f[B.grid_off + d * n3 + ((long long)cz[q] * B.n + cy[q]) * B.n + cx[q]] = accv[q][d];
+                part[d] += accv[q][d] - init[q][d];
+            }
+        }
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double v = part[d];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0)
+                red_sh[d][wid] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            double v = 0.0;
+            for (int q = 0; q < kDetThreads / 32; ++q)
+                v += red_sh[threadIdx.x][q];
+            w.red_tile[3LL * tile + threadIdx.x] = v * (1.0 / B.scale);
+        }
+    }
+}
+
+// ------------------------------------------------------------- interp
+// Thread per node (in tile order for locality). DET: the oracle's order,
+// acc = acc + ((phi_x*phi_y)*phi_z)*u from 0, z-outer, x-inner. Fast FP32:
+// separable sum_z phi_z sum_y phi_y sum_x phi_x u.
+template <typename real, bool DET, int KER>
+__global__ void __launch_bounds__(256) interp_kernel(DevBatch b, DevGrid g, DevWork w,
+                                                     const real *__restrict__ u, const real *__restrict__ x,
+                                                     real *__restrict__ v, real support, int use_order)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // in tile order only the binned nodes are listed (non-finite ones are not)
+    if (idx >= (use_order ? (long long)w.counters[5] : b.N))
+        return;
+    const int node = use_order ? w.own_nodes[idx] : (int)idx;
+    const InstDev I = b.inst[b.node_inst[node]];
+    const BoxDev B = g.boxes[I.box];
+    const long long N = b.N;
+    const long long n3 = (long long)B.n * B.n * B.n;
+    const int n = B.n;
+    real xl[3];
+    bool finite = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        xl[a] = x[a * N + node];
+        finite = finite && isfinite(xl[a]);
+    }
+    if (!finite) {
+        if (!use_order)
+            status_add(w.status, ST_DOMAIN, 1);
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            v[d * N + node] = xl[0] + xl[1] + xl[2];
+        return;
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const real *ud = u + B.grid_off + d * n3;
+        real out = real(0);
+        if constexpr (KER == 0) {
+            real ph[3][4];
+            int ix[4], iy[4], iz[4];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                int I0;
+                real s = LatCoord<real>::get(I, B, a, xl[a], (real)mac_off(d, a), I0);
+                long long i0 = peskin_axis<real>(s, ph[a]);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    int wi = wrapi(I0 + i0 + m, n);
+                    if (a == 0) ix[m] = wi;
+                    else if (a == 1) iy[m] = wi;
+                    else iz[m] = wi;
+                }
+            }
+            if (DET) {
+                real acc = real(0);
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+#pragma unroll
+                    for (int bb = 0; bb < 4; ++bb)
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            real wgt = (ph[0][a] * ph[1][bb]) * ph[2][c];
+                            acc = acc + wgt * ud[((long long)iz[c] * n + iy[bb]) * n + ix[a]];
+                        }
+                out = acc;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    real accz = real(0);
+#pragma unroll
+                    for (int bb = 0; bb < 4; ++bb) {
+                        const real *row = ud + ((long long)iz[c] * n + iy[bb]) * n;
+                        real accy = ph[0][0] * __ldg(row + ix[0]);
+#pragma unroll
+                        for (int a = 1; a < 4; ++a)
+                            accy += ph[0][a] * __ldg(row + ix[a]);
+                        accz += ph[1][bb] * accy;
+                    }
+                    out += ph[2][c] * accz;
+                }
+            }
+        } else {
+            real s[3];
+            int I0[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                s[a] = LatCoord<real>::get(I, B, a, xl[a], (real)mac_off(d, a), I0[a]);
+            int base[3];
+            real wt[27];
+            if (!mls_weights<real>(s, support, base, wt)) {
+                status_add(w.status, ST_DOMAIN, 1);
+                out = real(0);
+            } else {
+                real acc = real(0);
+                int J = 0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+                        for (int a = 0; a < 3; ++a, ++J) {
+                            long long gi = ((long long)wrapi((long long)I0[2] + base[2] + c, n) * n
+                                            + wrapi((long long)I0[1] + base[1] + bb, n)) * n
+                                           + wrapi((long long)I0[0] + base[0] + a, n);
+                            acc = acc + wt[J] * ud[gi];
+                        }
+                out = acc;
+            }
+        }
+        v[d * N + node] = out;
+    }
+}
+
+// ------------------------------------------------------------- reductions
+// Block per instance: FP64 sums in a fixed order (per-thread strided sums,
+// then a fixed shared-memory tree). Layout: 12 doubles per instance.
+template <int NT>
+__device__ inline double block_sum(double v, double *sh)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+#pragma unroll
+    for (int s = NT / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) reduce_inst_kernel(DevBatch b, const real *__restrict__ x,
+                                                          const real *__restrict__ F,
+                                                          const real *__restrict__ v, double *__restrict__ red)
+{
+    __shared__ double sh[256];
+    const InstDev I = b.inst[blockIdx.x];
+    const long long N = b.N;
+    double c[3];
+    for (int a = 0; a < 3; ++a) {
+        double s = 0.0;
+        for (int k = threadIdx.x; k < I.n_nodes; k += blockDim.x)
+            s += (double)x[a * N + I.node_off + k];
+        c[a] = block_sum<256>(s, sh) / (double)I.n_nodes;
+    }
+    double out[12] = {c[0], c[1], c[2], 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double p[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = threadIdx.x; k < I.n_nodes; k += blockDim.x) {
+        const int node = I.node_off + k;
+        double r[3], Fk[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            r[a] = (double)x[a * N + node] - c[a];
+            Fk[a] = F ? (double)F[a * N + node] : 0.0;
+            p[a] += Fk[a];
+            p[6 + a] += v ? (double)v[a * N + node] : 0.0;
+        }
+        p[3] += r[1] * Fk[2] - r[2] * Fk[1];
+        p[4] += r[2] * Fk[0] - r[0] * Fk[2];
+        p[5] += r[0] * Fk[1] - r[1] * Fk[0];
+    }
+    for (int q = 0; q < 9; ++q)
+        out[3 + q] = block_sum<256>(p[q], sh);
+    if (threadIdx.x < 12)
+        red[12LL * blockIdx.x + threadIdx.x] = out[threadIdx.x];
+}
+
+// Block per box: h^3 * sum of the values added by the last spread, from the
+// per-tile FP64 partials, in tile order.
+static __global__ void __launch_bounds__(256) reduce_box_kernel(DevGrid g, const double *__restrict__ red_tile,
+                                                         double *__restrict__ red_box)
+{
+    __shared__ double sh[256];
+    const BoxDev B = g.boxes[blockIdx.x];
+    const long long nt = (long long)B.T * B.T * B.T;
+    for (int d = 0; d < 3; ++d) {
+        double s = 0.0;
+        for (long long t = threadIdx.x; t < nt; t += blockDim.x)
+            s += red_tile[3 * (B.tile_base + t) + d];
+        double r = block_sum<256>(s, sh);
+        if (threadIdx.x == 0) {
+            red_box[6LL * blockIdx.x + d] = r;
+            red_box[6LL * blockIdx.x + 3 + d] = 0.0;
+        }
+    }
+}
+
+}  // namespace ifem

@@ -1,0 +1,224 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+FP64 (deterministic) mode: element forces, nodal sums, spreading and
+interpolation must be bit-identical to the oracle; the bending force (which
+uses atan2) must agree to 1e-12 relative L2.
+FP32 mode: relative L2 error against the oracle evaluated on the same
+FP32-rounded inputs within 1e-5 (forces, spread field) and 1e-6 (interpolated
+velocities).
+"""
+import numpy as np
+import pytest
+
+import ifem_workloads as W
+from oracle import oracle as O
+from tests._helpers import oracle_step, random_grid, rel_l2, rounded_workload, run_gpu_step
+
+pytestmark = pytest.mark.gpu
+
+FP32, FP64 = 0, 1
+TOL_F, TOL_V, TOL_GRID = 1e-5, 1e-6, 1e-5
+
+_cache = {}
+
+
+def wl(name, **kw):
+    key = (name, tuple(sorted(kw.items())))
+    if key not in _cache:
+        _cache[key] = W.make(name, **kw)
+    return _cache[key]
+
+
+def no_bending(w):
+    import dataclasses
+    return dataclasses.replace(w, templates=[dataclasses.replace(t, kb=0.0) for t in w.templates])
+
+
+# ------------------------------------------------------------------ FP64
+@pytest.mark.parametrize("case", ["C1-nh", "C1-skalak", "C2-elastic", "C3"])
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_fp64_step_bit_exact(case, kernel):
+    if case.startswith("C1"):
+        w = wl("C1", law=case.split("-")[1])
+    elif case == "C2-elastic":
+        w = no_bending(wl("C2"))
+    else:
+        w = wl("C3")
+    f0 = random_grid(w, seed=3)
+    g = run_gpu_step(w, FP64, kernel=kernel, f0=f0)
+    o = oracle_step(w, kernel=kernel, f0=f0)
+    assert g["rc"] == 0, g["stats"]
+    assert np.array_equal(g["F"], o["F"]), np.abs(g["F"] - o["F"]).max()
+    assert np.array_equal(g["v"], o["v"]), np.abs(g["v"] - o["v"]).max()
+    for gb, ob in zip(g["f"], o["f"]):
+        assert np.array_equal(gb, ob), np.abs(gb - ob).max()
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_fp64_bending_step(kernel):
+    w = wl("C2")
+    g = run_gpu_step(w, FP64, kernel=kernel)
+    o = oracle_step(w, kernel=kernel)
+    assert rel_l2(g["F"], o["F"]) < 1e-12
+    assert rel_l2(g["v"], o["v"]) == 0.0
+    assert rel_l2(g["f"][0], o["f"][0]) < 1e-12
+
+
+def test_fp64_deterministic_across_runs():
+    w = wl("C2")
+    a = run_gpu_step(w, FP64)
+    b = run_gpu_step(w, FP64)
+    for k in ("F", "v"):
+        assert np.array_equal(a[k], b[k])
+    assert np.array_equal(a["f"][0], b["f"][0])
+    assert np.array_equal(a["red"], b["red"])
+
+
+@pytest.mark.parametrize("flags", [1, 2, 3])
+def test_fp64_spread_modes(flags):
+    """force form (1), overwrite (2) and both (3) against the oracle."""
+    w = wl("C1")
+    f0 = random_grid(w, seed=5)
+    g = run_gpu_step(w, FP64, flags=flags, f0=f0)
+    o = oracle_step(w, density=not (flags & 1), f0=None if flags & 2 else f0)
+    assert np.array_equal(g["f"][0], o["f"][0])
+
+
+# ------------------------------------------------------------------ FP32
+@pytest.mark.parametrize("case", ["C1", "C2", "C3"])
+@pytest.mark.parametrize("scatter", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_fp32_step_tolerances(case, scatter, kernel):
+    w = rounded_workload(wl(case), np.float32)
+    g = run_gpu_step(w, FP32, kernel=kernel, scatter=scatter)
+    o = oracle_step(w, kernel=kernel)
+    assert g["rc"] == 0, g["stats"]
+    eF, ev, ef = rel_l2(g["F"], o["F"]), rel_l2(g["v"], o["v"]), rel_l2(g["f"][0], o["f"][0])
+    assert eF < TOL_F and ev < TOL_V and ef < TOL_GRID, (eF, ev, ef)
+
+
+def test_fp32_det_scatter_reproducible():
+    w = wl("C2")
+    a = run_gpu_step(w, FP32, scatter=0)
+    b = run_gpu_step(w, FP32, scatter=0)
+    assert np.array_equal(a["F"], b["F"])
+    assert np.array_equal(a["v"], b["v"])
+
+
+# ------------------------------------------------------------------ reductions
+@pytest.mark.parametrize("precision", [FP32, FP64])
+def test_reductions(precision):
+    w = wl("C2")
+    if precision == FP32:
+        w = rounded_workload(w, np.float32)
+    g = run_gpu_step(w, precision)
+    red = g["red"]
+    ni = len(w.instances)
+    xl = w.x_local_all()
+    exp = O.reductions(w, xl, g["F"], g["v"])
+    got = red[: 12 * ni].reshape(ni, 12)
+    scale = np.array([np.abs(xl).max()] * 3 + [np.abs(g["F"]).max() * len(xl)] * 3
+                     + [np.abs(g["F"]).max() * np.abs(xl).max() * len(xl)] * 3 + [np.abs(g["v"]).max() * len(xl)] * 3)
+    assert np.all(np.abs(got - exp) <= 1e-13 * scale + 1e-300)
+    # grid side: h^3 sum of the spread values equals the total nodal force
+    box = red[12 * ni: 12 * ni + 3]
+    tol = 1e-11 if precision == FP64 else 1e-5
+    np.testing.assert_allclose(box, exp[0, 3:6], atol=tol * np.abs(g["F"]).sum(0).max())
+
+
+# ------------------------------------------------------------------ HVP
+def _hvp_gpu(w, precision, wvec):
+    import torch
+    from paper_1807_08219_gb300 import ifem as I
+    cp = I.Coupler(w, precision=precision)
+    try:
+        x = cp.nodes_to_device(w.x_local_all())
+        wd = cp.nodes_to_device(wvec)
+        Hw = cp.empty_nodes()
+        I.ifem_force_hvp(cp.ctx, cp.batch, x, wd, Hw)
+        torch.cuda.synchronize()
+        return cp.nodes_to_host(Hw)
+    finally:
+        cp.close()
+
+
+@pytest.mark.parametrize("case", ["C1-nh", "C1-skalak", "C3"])
+@pytest.mark.parametrize("precision", [FP32, FP64])
+def test_hvp_vs_oracle(case, precision):
+    w = wl("C1", law=case.split("-")[1]) if case.startswith("C1") else wl("C3")
+    if precision == FP32:
+        w = rounded_workload(w, np.float32)
+    tm = w.templates[0]
+    wvec = np.random.default_rng(2).standard_normal((w.n_nodes, 3))
+    if precision == FP32:
+        wvec = wvec.astype(np.float32).astype(np.float64)
+    g = _hvp_gpu(w, precision, wvec)
+    x = w.x_local_all()
+    if tm.kind == "membrane":
+        o = O.membrane_hvp(tm.law, tm.mu, tm.C, tm.elems, tm.X, x, wvec)
+    else:
+        o = O.tet_hvp(tm.lam, tm.mu, tm.elems, tm.X, x, wvec)
+    assert rel_l2(g, o) < (1e-12 if precision == FP64 else 1e-4)
+
+
+# ------------------------------------------------------------------ edge cases
+def test_particle_across_periodic_boundary_and_outside_box():
+    """Origins near the box faces and outside [0, L): wrap must match the oracle."""
+    import dataclasses
+    w = wl("C1")
+    for org in ([0.999, 0.0005, 0.5], [1.3, -0.2, 5.0]):
+        ww = dataclasses.replace(w, instances=[dataclasses.replace(w.instances[0], origin=np.array(org))])
+        g = run_gpu_step(ww, FP64)
+        o = oracle_step(ww)
+        assert np.array_equal(g["v"], o["v"])
+        assert np.array_equal(g["f"][0], o["f"][0])
+
+
+def test_small_box_ragged_tiles():
+    """A 9^3 box (single ragged tile per axis at t = 8) and a 27^3 box (ragged last tile)."""
+    import dataclasses
+    base = wl("C1")
+    for n, scale in ((9, 0.02), (27, 0.06)):
+        tm = dataclasses.replace(base.templates[0], X=base.templates[0].X * scale / 0.15)
+        inst = dataclasses.replace(base.instances[0], x_local=base.instances[0].x_local * scale / 0.15)
+        u = np.random.default_rng(n).standard_normal((3, n, n, n))
+        ww = dataclasses.replace(base, templates=[tm], instances=[inst], boxes=[W.Box(n, 1.0)], u=[u])
+        for tile in (6, 8):
+            g = run_gpu_step(ww, FP64, tile=tile)
+            o = oracle_step(ww)
+            assert np.array_equal(g["f"][0], o["f"][0])
+            assert np.array_equal(g["v"], o["v"])
+
+
+def test_empty_batch():
+    import dataclasses
+    w = dataclasses.replace(wl("C1"), instances=[])
+    f0 = random_grid(w, seed=1)
+    g = run_gpu_step(w, FP64, f0=f0)
+    assert g["rc"] == 0
+    assert np.array_equal(g["f"][0], f0[0])
+
+
+def test_nan_position_reports_domain_error():
+    import dataclasses
+    w = wl("C1")
+    x = w.instances[0].x_local.copy()
+    x[5, 1] = np.nan
+    ww = dataclasses.replace(w, instances=[dataclasses.replace(w.instances[0], x_local=x)])
+    g = run_gpu_step(ww, FP32)
+    assert g["rc"] == -6 and g["stats"]["domain_errors"] >= 1
+
+
+def test_inverted_tet_is_counted_and_still_evaluated():
+    import dataclasses
+    w = wl("C3")
+    tm = w.templates[0]
+    x = w.instances[0].x_local.copy()
+    t0 = tm.elems[100]
+    x[t0[0]] = x[t0[1]] + 2.0 * (x[t0[0]] - x[t0[1]]) * -1.0
+    ww = dataclasses.replace(w, instances=[dataclasses.replace(w.instances[0], x_local=x)])
+    g = run_gpu_step(ww, FP64)
+    F, ninv = O.tet_forces(tm.lam, tm.mu, tm.elems, tm.X, x, return_inverted=True)
+    assert ninv >= 1
+    assert g["rc"] == -5 and g["stats"]["inverted_elements"] == ninv
+    assert np.array_equal(g["F"], F)
