@@ -91,9 +91,13 @@ class Workload:
 
     def x_local_all(self, dtype=np.float64) -> np.ndarray:
         """(N, 3) concatenated local positions, rounded to dtype."""
+        if not self.instances:
+            return np.zeros((0, 3), dtype=dtype)
         return np.concatenate([i.x_local for i in self.instances]).astype(dtype)
 
     def origins_per_node(self) -> np.ndarray:
+        if not self.instances:
+            return np.zeros((0, 3))
         return np.concatenate([np.broadcast_to(i.origin, (self.templates[i.tmpl].n_nodes, 3))
                                for i in self.instances])
 
