@@ -9,6 +9,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <set>
@@ -31,6 +32,7 @@ struct ifem_ctx_s {
     cudaEvent_t ev[6] = {};
     int ev_ok = 0;
     int ev_recorded = 0;
+    int acc64 = 1;
 };
 
 struct ifem_tmpl_s {
@@ -151,6 +153,10 @@ extern "C" int ifem_ctx_create(const ifem_config *cfg, ifem_ctx *out)
     if (!(ctx->cfg.mls_support > 0.0))
         ctx->cfg.mls_support = std::sqrt(3.0);
     ctx->tile = cfg->tile ? cfg->tile : 8;
+    // FP32 spread accumulator width (tuning knob): IFEM_SPREAD_ACC=32 selects
+    // 32-bit fixed point, anything else 64-bit
+    if (const char *acc = std::getenv("IFEM_SPREAD_ACC"))
+        ctx->acc64 = std::string(acc) == "32" ? 0 : 1;
     if (cudaSetDevice(cfg->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, cfg->device) != cudaSuccess ||
         cudaMalloc((void **)&ctx->d_status, sizeof(unsigned long long) * kStatusWords) != cudaSuccess ||
@@ -755,6 +761,7 @@ static TransferArgs transfer_args(ifem_ctx ctx, ifem_batch b, const void *x, con
     a.density = (flags & IFEM_SPREAD_FORCE) ? 0 : 1;
     a.support = ctx->cfg.mls_support;
     a.n_sm = ctx->n_sm;
+    a.acc64 = ctx->acc64;
     a.stream = (cudaStream_t)stream;
     return a;
 }

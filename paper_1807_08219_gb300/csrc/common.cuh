@@ -296,6 +296,7 @@ struct TransferArgs {
     int density;
     double support;
     int n_sm;
+    int acc64;        // FP32 spread: 64-bit (1) or 32-bit (0) fixed-point accumulators
     cudaStream_t stream;
 };
 

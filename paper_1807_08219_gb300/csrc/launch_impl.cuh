@@ -99,8 +99,11 @@ cudaError_t spread_impl(const TransferArgs &a)
         return cudaSuccess;
     if constexpr (std::is_same<real, float>::value) {
         const int E = a.g.max_edge;
-        size_t sm = sizeof(float) * 3 * (size_t)E * E * E;
-        auto kern = a.kernel == 0 ? spread_fast_kernel<0> : spread_fast_kernel<1>;
+        cudaMemsetAsync(a.w.counters + 2, 0, sizeof(int), s);
+        size_t acc = a.acc64 ? sizeof(long long) : sizeof(int);
+        size_t sm = acc * 3 * (size_t)E * E * E;
+        auto kern = a.kernel == 0 ? (a.acc64 ? spread_fast_kernel<0, long long> : spread_fast_kernel<0, int>)
+                                  : (a.acc64 ? spread_fast_kernel<1, long long> : spread_fast_kernel<1, int>);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         int occ = 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, sm);
@@ -125,15 +128,26 @@ cudaError_t interp_impl(const TransferArgs &a)
     const DevBatch &b = a.b;
     if (b.n_inst == 0 || b.N == 0)
         return cudaSuccess;
-    constexpr bool DET = std::is_same<real, double>::value;
-    unsigned grid = (unsigned)((b.N + 255) / 256);
-    int use_order = DET ? 0 : 1;
-    if (a.kernel == 0)
-        interp_kernel<real, DET, 0><<<grid, 256, 0, a.stream>>>(b, a.g, a.w, (const real *)a.u, (const real *)a.x,
-                                                              (real *)a.v, (real)a.support, use_order);
-    else
-        interp_kernel<real, DET, 1><<<grid, 256, 0, a.stream>>>(b, a.g, a.w, (const real *)a.u, (const real *)a.x,
-                                                              (real *)a.v, (real)a.support, use_order);
+    if constexpr (std::is_same<real, float>::value) {
+        const int E = a.g.max_edge + 4;
+        size_t sm = sizeof(float) * 3 * (size_t)E * E * E;
+        cudaMemsetAsync(a.w.counters + 3, 0, sizeof(int), a.stream);
+        auto kern = a.kernel == 0 ? interp_tile_kernel<0> : interp_tile_kernel<1>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        int occ = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, sm);
+        occ = occ < 1 ? 1 : occ;
+        kern<<<a.n_sm * occ, 256, sm, a.stream>>>(b, a.g, a.w, (const float *)a.u, (const float *)a.x, (float *)a.v,
+                                                  (float)a.support);
+    } else {
+        unsigned grid = (unsigned)((b.N + 255) / 256);
+        if (a.kernel == 0)
+            interp_kernel<real, true, 0><<<grid, 256, 0, a.stream>>>(b, a.g, a.w, (const real *)a.u,
+                                                                    (const real *)a.x, (real *)a.v, (real)a.support, 0);
+        else
+            interp_kernel<real, true, 1><<<grid, 256, 0, a.stream>>>(b, a.g, a.w, (const real *)a.u,
+                                                                    (const real *)a.x, (real *)a.v, (real)a.support, 0);
+    }
     IFEM_LAUNCH_CHECK();
     return cudaSuccess;
 }

@@ -302,137 +302,226 @@ __device__ __forceinline__ long long peskin_axis(real s, real ph[4])
 }
 
 // ---------------------------------------------------- spread, FP32 fast
-// One CTA per active tile (grid-stride over the active list). Shared
-// memory: the tile's owned values of the three lattices, accumulated with
-// shared-memory atomics; flushed with one read-modify-write per non-zero
-// value. Per-tile FP64 sums of the added values go to red_tile[3*tile + d].
-template <int KER>
+// One CTA per active tile, tiles taken from a global counter. Contributions
+// are accumulated in shared memory as fixed-point integers (Acc = int or
+// long long) with native integer atomics: integer addition is associative,
+// so the accumulated tile is independent of the order in which threads add
+// (the FP32 result is reproducible run to run). Per tile and lattice the
+// scale is a power of two chosen from a bound on the largest possible sum,
+// |f_J| <= wmax * sum_k |g_k| over the tile's candidates, so no sum can
+// overflow. Work units are (candidate node, lattice) pairs. Flush: one
+// read-modify-write per non-zero owned value, rows of x in lanes.
+template <typename Acc>
+struct FixedPoint;
+template <>
+struct FixedPoint<int> {
+    static constexpr float kRange = 1073741824.0f;  // 2^30
+    __device__ static __forceinline__ int conv(float v) { return __float2int_rn(v); }
+};
+template <>
+struct FixedPoint<long long> {
+    static constexpr float kRange = 1152921504606846976.0f;  // 2^60
+    __device__ static __forceinline__ long long conv(float v) { return __float2ll_rn(v); }
+};
+
+__device__ __forceinline__ void acc_add(int *p, int v) { atomicAdd(p, v); }
+// two's-complement addition through the unsigned 64-bit atomic
+__device__ __forceinline__ void acc_add(long long *p, long long v)
+{
+    atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+}
+
+// n-periodic wrap of an index that is normally already in (-n, 2n)
+__device__ __forceinline__ int wrap_near(int v, int n)
+{
+    if (v < 0)
+        v += n;
+    else if (v >= n)
+        v -= n;
+    if ((unsigned)v >= (unsigned)n)
+        v = wrapi(v, n);
+    return v;
+}
+
+template <int KER, typename Acc>
 __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g, DevWork w,
                                                           const float *__restrict__ x,
                                                           const float *__restrict__ F, float *__restrict__ f,
                                                           int density, float support)
 {
-    extern __shared__ float acc[];
+    extern __shared__ __align__(16) unsigned char spread_smem[];
+    Acc *acc = reinterpret_cast<Acc *>(spread_smem);
+    __shared__ float s_part[3][8];
+    __shared__ float s_scale[3];
     __shared__ double red_sh[3][8];
+    __shared__ int s_tile;
     const long long N = b.N;
     const int n_active = w.counters[0];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         status_add(w.status, ST_PAIRS, (unsigned long long)w.cand_off[g.n_tiles]);
         status_add(w.status, ST_ACTIVE, (unsigned long long)n_active);
     }
-    for (int it = blockIdx.x; it < n_active; it += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_tile = atomicAdd(&w.counters[2], 1);
+        __syncthreads();
+        const int it = s_tile;
+        if (it >= n_active)
+            break;
         const int tile = w.active[it];
         const TileInfo ti = decode_tile(g, tile);
         const BoxDev B = g.boxes[ti.box];
         const int ex = ti.edge[0], ey = ti.edge[1], ez = ti.edge[2];
         const int vol = ex * ey * ez;
+        const int n = B.n;
         for (int i = threadIdx.x; i < 3 * vol; i += blockDim.x)
-            acc[i] = 0.f;
-        __syncthreads();
-        const float scale = density ? (float)B.scale : 1.f;
+            acc[i] = 0;
+        const float sd = density ? (float)B.scale : 1.f;
         const int beg = w.cand_off[tile], end = w.cand_off[tile + 1];
+        const int nc = end - beg;
+        // bound on |sum| per lattice: wmax * sum_k |F_k,d| * sd
+        float gs[3] = {0.f, 0.f, 0.f};
         for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
             const int node = w.cand_nodes[q];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                gs[d] += fabsf(F[d * N + node]);
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            float v = gs[d];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0)
+                s_part[d][wid] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            float tot = 0.f;
+            for (int q = 0; q < nw; ++q)
+                tot += s_part[threadIdx.x][q];
+            const float wmax = KER == 0 ? 0.125f : 2.0f;
+            float bound = tot * sd * wmax * 1.0001f;
+            float sc = 1.f;
+            if (bound > 0.f && isfinite(bound)) {
+                int e = (int)floorf(log2f(FixedPoint<Acc>::kRange / bound));
+                e = e > 120 ? 120 : (e < -120 ? -120 : e);
+                sc = exp2f((float)e);
+            }
+            s_scale[threadIdx.x] = sc;
+        }
+        __syncthreads();
+        for (int u = threadIdx.x; u < 3 * nc; u += blockDim.x) {
+            const int d = u / nc;
+            const int j = u - d * nc;
+            const int node = w.cand_nodes[beg + j];
             const InstDev I = b.inst[b.node_inst[node]];
-            float xl[3];
+            const float gq = F[d * N + node] * sd * s_scale[d];
+            Acc *accd = acc + d * vol;
+            if constexpr (KER == 0) {
+                float ph[3][4];
+                int loc[3][4];
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
-                xl[a] = x[a * N + node];
+                for (int a = 0; a < 3; ++a) {
+                    int I0;
+                    float s = LatCoord<float>::get(I, B, a, x[a * N + node], mac_off(d, a), I0);
+                    int i0 = (int)floorf(s) - 1;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const float gd = F[d * N + node] * scale;
-                float* accd = acc + d * vol;
-                if constexpr (KER == 0) {
-                    float ph[3][4];
-                    int loc[3][4];
+                    for (int m = 0; m < 4; ++m)
+                        ph[a][m] = phi4<float>(s - (float)(i0 + m));
+                    int base = wrap_near(I0 + i0, n);
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        int I0;
-                        float s = LatCoord<float>::get(I, B, a, xl[a], mac_off(d, a), I0);
-                        long long i0 = peskin_axis<float>(s, ph[a]);
-#pragma unroll
-                        for (int m = 0; m < 4; ++m) {
-                            int l = wrapi(I0 + i0 + m, B.n) - ti.start[a];
-                            loc[a][m] = (l >= 0 && l < ti.edge[a]) ? l : -1;
-                        }
+                    for (int m = 0; m < 4; ++m) {
+                        int idx = base + m;
+                        idx -= idx >= n ? n : 0;
+                        loc[a][m] = idx - ti.start[a];
                     }
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        if (loc[2][c] < 0)
-                            continue;
-#pragma unroll
-                        for (int bb = 0; bb < 4; ++bb) {
-                            if (loc[1][bb] < 0)
-                                continue;
-                            const float wyz = ph[1][bb] * ph[2][c] * gd;
-                            const int row = (loc[2][c] * ey + loc[1][bb]) * ex;
-#pragma unroll
-                            for (int a = 0; a < 4; ++a)
-                                if (loc[0][a] >= 0)
-                                    atomicAdd(&accd[row + loc[0][a]], ph[0][a] * wyz);
-                        }
-                    }
-                } else {
-                    float s[3];
-                    int I0[3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-                        s[a] = LatCoord<float>::get(I, B, a, xl[a], mac_off(d, a), I0[a]);
-                    int base[3];
-                    float wt[27];
-                    if (!mls_weights<float>(s, support, base, wt)) {
-                        status_add(w.status, ST_DOMAIN, 1);
-                        continue;
-                    }
-                    int loc[3][3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-#pragma unroll
-                        for (int m = 0; m < 3; ++m) {
-                            int l = wrapi((long long)I0[a] + base[a] + m, B.n) - ti.start[a];
-                            loc[a][m] = (l >= 0 && l < ti.edge[a]) ? l : -1;
-                        }
-                    int J = 0;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-#pragma unroll
-                        for (int bb = 0; bb < 3; ++bb)
-#pragma unroll
-                            for (int a = 0; a < 3; ++a, ++J)
-                                if (loc[2][c] >= 0 && loc[1][bb] >= 0 && loc[0][a] >= 0)
-                                    atomicAdd(&accd[(loc[2][c] * ey + loc[1][bb]) * ex + loc[0][a]], wt[J] * gd);
                 }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if ((unsigned)loc[2][c] >= (unsigned)ez)
+                        continue;
+                    const float wz = ph[2][c] * gq;
+#pragma unroll
+                    for (int bb = 0; bb < 4; ++bb) {
+                        if ((unsigned)loc[1][bb] >= (unsigned)ey)
+                            continue;
+                        const float wyz = ph[1][bb] * wz;
+                        Acc *row = accd + (loc[2][c] * ey + loc[1][bb]) * ex;
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+                            if ((unsigned)loc[0][a] < (unsigned)ex)
+                                acc_add(row + loc[0][a], FixedPoint<Acc>::conv(ph[0][a] * wyz));
+                    }
+                }
+            } else {
+                float s[3];
+                int I0[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    s[a] = LatCoord<float>::get(I, B, a, x[a * N + node], mac_off(d, a), I0[a]);
+                int base[3];
+                float wt[27];
+                if (!mls_weights<float>(s, support, base, wt)) {
+                    status_add(w.status, ST_DOMAIN, 1);
+                    continue;
+                }
+                int loc[3][3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    int bw = wrap_near(I0[a] + base[a], n);
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {
+                        int idx = bw + m;
+                        idx -= idx >= n ? n : 0;
+                        loc[a][m] = idx - ti.start[a];
+                    }
+                }
+                int J = 0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+#pragma unroll
+                    for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+                        for (int a = 0; a < 3; ++a, ++J)
+                            if ((unsigned)loc[2][c] < (unsigned)ez && (unsigned)loc[1][bb] < (unsigned)ey &&
+                                (unsigned)loc[0][a] < (unsigned)ex)
+                                acc_add(accd + (loc[2][c] * ey + loc[1][bb]) * ex + loc[0][a],
+                                        FixedPoint<Acc>::conv(wt[J] * gq));
             }
         }
         __syncthreads();
-        // flush: f += acc for every non-zero owned value; FP64 tile sums
-        const long long n3 = (long long)B.n * B.n * B.n;
+        // flush: rows (d, z, y) over warps, x over lanes
+        const long long n3 = (long long)n * n * n;
         double part[3] = {0.0, 0.0, 0.0};
         unsigned long long touched = 0;
-        for (int d = 0; d < 3; ++d) {
-            float *fd = f + B.grid_off + d * n3;
-            for (int i = threadIdx.x; i < vol; i += blockDim.x) {
-                float v = acc[d * vol + i];
-                if (v != 0.f) {
-                    int lx = i % ex, ly = (i / ex) % ey, lz = i / (ex * ey);
-                    long long gi = ((long long)(ti.start[2] + lz) * B.n + (ti.start[1] + ly)) * B.n
-                                   + (ti.start[0] + lx);
-                    fd[gi] += v;
-                    part[d] += (double)v;
+        const int rows_per_d = ey * ez;
+        for (int r = wid; r < 3 * rows_per_d; r += nw) {
+            const int d = r / rows_per_d;
+            const int rem = r - d * rows_per_d;
+            const int lz = rem / ey, ly = rem - lz * ey;
+            const float inv = 1.f / s_scale[d];
+            const Acc *src = acc + d * vol + (lz * ey + ly) * ex;
+            float *dst = f + B.grid_off + d * n3 + ((long long)(ti.start[2] + lz) * n + (ti.start[1] + ly)) * n
+                         + ti.start[0];
+            for (int lx = lane; lx < ex; lx += 32) {
+                const Acc q = src[lx];
+                if (q != 0) {
+                    const float val = (float)q * inv;
+                    dst[lx] += val;
+                    part[d] += (double)val;
                     ++touched;
                 }
             }
         }
-        // fixed-order block reduction of part[]; count of touched values
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        {
-            unsigned long long cnt = touched;
+        unsigned long long cnt = touched;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-                cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-            if (lane == 0)
-                status_add(w.status, ST_TOUCHED, cnt);
-        }
+        for (int o = 16; o > 0; o >>= 1)
+            cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+        if (lane == 0)
+            status_add(w.status, ST_TOUCHED, cnt);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             double v = part[d];
@@ -445,11 +534,126 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
         __syncthreads();
         if (threadIdx.x < 3) {
             double v = 0.0;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
+            for (int q = 0; q < nw; ++q)
                 v += red_sh[threadIdx.x][q];
             w.red_tile[3LL * tile + threadIdx.x] = v * (1.0 / B.scale);
         }
+        // the next iteration's first barrier orders these reads before s_tile/acc are rewritten
+    }
+}
+
+// ------------------------------------------------------- interp, FP32 fast
+// One CTA per tile with own nodes (tiles from a global counter): the tile's
+// velocity footprint (tile + 2 cells of halo per side, three lattices) is
+// staged in shared memory with coalesced row loads, then every (node,
+// lattice) unit gathers its stencil from shared memory:
+// v = sum_z phi_z sum_y phi_y sum_x phi_x u.
+template <int KER>
+__global__ void __launch_bounds__(256) interp_tile_kernel(DevBatch b, DevGrid g, DevWork w,
+                                                          const float *__restrict__ u,
+                                                          const float *__restrict__ x, float *__restrict__ v,
+                                                          float support)
+{
+    extern __shared__ __align__(16) float us[];
+    __shared__ int s_tile;
+    const long long N = b.N;
+    const int n_tiles = w.counters[1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_tile = atomicAdd(&w.counters[3], 1);
         __syncthreads();
+        const int it = s_tile;
+        if (it >= n_tiles)
+            break;
+        const int tile = w.own_active[it];
+        const TileInfo ti = decode_tile(g, tile);
+        const BoxDev B = g.boxes[ti.box];
+        const int n = B.n;
+        const int fx = ti.edge[0] + 4, fy = ti.edge[1] + 4, fz = ti.edge[2] + 4;
+        const int fvol = fx * fy * fz;
+        const long long n3 = (long long)n * n * n;
+        // stage: rows (d, z, y) over warps, x over lanes
+        for (int r = wid; r < 3 * fy * fz; r += nw) {
+            const int d = r / (fy * fz);
+            const int rem = r - d * fy * fz;
+            const int lz = rem / fy, ly = rem - lz * fy;
+            const int gz = wrap_near(ti.start[2] - 2 + lz, n), gy = wrap_near(ti.start[1] - 2 + ly, n);
+            const float *row = u + B.grid_off + d * n3 + ((long long)gz * n + gy) * n;
+            float *dst = us + d * fvol + (lz * fy + ly) * fx;
+            for (int lx = lane; lx < fx; lx += 32)
+                dst[lx] = __ldg(row + wrap_near(ti.start[0] - 2 + lx, n));
+        }
+        __syncthreads();
+        const int beg = w.own_off[tile], cnt = w.own_off[tile + 1] - beg;
+        for (int q = threadIdx.x; q < 3 * cnt; q += blockDim.x) {
+            const int d = q / cnt;
+            const int node = w.own_nodes[beg + q - d * cnt];
+            const InstDev I = b.inst[b.node_inst[node]];
+            const float *ud = us + d * fvol;
+            float out = 0.f;
+            if constexpr (KER == 0) {
+                float ph[3][4];
+                int l0[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    int I0;
+                    float s = LatCoord<float>::get(I, B, a, x[a * N + node], mac_off(d, a), I0);
+                    int i0 = (int)floorf(s) - 1;
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        ph[a][m] = phi4<float>(s - (float)(i0 + m));
+                    int l = wrap_near(I0 + i0, n) - (ti.start[a] - 2);
+                    l += l < 0 ? n : 0;
+                    l -= l >= n ? n : 0;
+                    l0[a] = l;
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float accz = 0.f;
+#pragma unroll
+                    for (int bb = 0; bb < 4; ++bb) {
+                        const float *row = ud + ((l0[2] + c) * fy + (l0[1] + bb)) * fx + l0[0];
+                        float accy = ph[0][0] * row[0];
+#pragma unroll
+                        for (int a = 1; a < 4; ++a)
+                            accy += ph[0][a] * row[a];
+                        accz += ph[1][bb] * accy;
+                    }
+                    out += ph[2][c] * accz;
+                }
+            } else {
+                float s[3];
+                int I0[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    s[a] = LatCoord<float>::get(I, B, a, x[a * N + node], mac_off(d, a), I0[a]);
+                int base[3];
+                float wt[27];
+                if (!mls_weights<float>(s, support, base, wt)) {
+                    status_add(w.status, ST_DOMAIN, 1);
+                } else {
+                    int l0[3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        int l = wrap_near(I0[a] + base[a], n) - (ti.start[a] - 2);
+                        l += l < 0 ? n : 0;
+                        l -= l >= n ? n : 0;
+                        l0[a] = l;
+                    }
+                    int J = 0;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+#pragma unroll
+                        for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+                            for (int a = 0; a < 3; ++a, ++J)
+                                out += wt[J] * ud[((l0[2] + c) * fy + (l0[1] + bb)) * fx + l0[0] + a];
+                }
+            }
+            v[d * N + node] = out;
+        }
+        // the next iteration's first barrier orders these reads before us is rewritten
     }
 }
 
@@ -770,41 +974,72 @@ __device__ inline double block_sum(double v, double *sh)
     return r;
 }
 
+// One pass per instance: FP64 partial sums of x, F, v and x (x) F (about the
+// instance's local origin) per thread, then a fixed-order warp/CTA tree.
+// Torque about the centroid: sum (x - c) x F = sum x x F - c x sum F.
 template <typename real>
 __global__ void __launch_bounds__(256) reduce_inst_kernel(DevBatch b, const real *__restrict__ x,
                                                           const real *__restrict__ F,
                                                           const real *__restrict__ v, double *__restrict__ red)
 {
-    __shared__ double sh[256];
+    __shared__ double sh[12][8];
     const InstDev I = b.inst[blockIdx.x];
     const long long N = b.N;
-    double c[3];
-    for (int a = 0; a < 3; ++a) {
-        double s = 0.0;
-        for (int k = threadIdx.x; k < I.n_nodes; k += blockDim.x)
-            s += (double)x[a * N + I.node_off + k];
-        c[a] = block_sum<256>(s, sh) / (double)I.n_nodes;
-    }
-    double out[12] = {c[0], c[1], c[2], 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    double p[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double p[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q)
+        p[q] = 0.0;
     for (int k = threadIdx.x; k < I.n_nodes; k += blockDim.x) {
         const int node = I.node_off + k;
-        double r[3], Fk[3];
+        double xk[3], Fk[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            r[a] = (double)x[a * N + node] - c[a];
+            xk[a] = (double)x[a * N + node];
             Fk[a] = F ? (double)F[a * N + node] : 0.0;
-            p[a] += Fk[a];
-            p[6 + a] += v ? (double)v[a * N + node] : 0.0;
+            p[a] += xk[a];
+            p[3 + a] += Fk[a];
+            p[9 + a] += v ? (double)v[a * N + node] : 0.0;
         }
-        p[3] += r[1] * Fk[2] - r[2] * Fk[1];
-        p[4] += r[2] * Fk[0] - r[0] * Fk[2];
-        p[5] += r[0] * Fk[1] - r[1] * Fk[0];
+        p[6] += xk[1] * Fk[2] - xk[2] * Fk[1];
+        p[7] += xk[2] * Fk[0] - xk[0] * Fk[2];
+        p[8] += xk[0] * Fk[1] - xk[1] * Fk[0];
     }
-    for (int q = 0; q < 9; ++q)
-        out[3 + q] = block_sum<256>(p[q], sh);
-    if (threadIdx.x < 12)
-        red[12LL * blockIdx.x + threadIdx.x] = out[threadIdx.x];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+        double t = p[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0)
+            sh[q][wid] = t;
+    }
+    __syncthreads();
+    __shared__ double tot[12];
+    if (threadIdx.x < 12) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
+            t += sh[threadIdx.x][q];
+        tot[threadIdx.x] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double *o = red + 12LL * blockIdx.x;
+        double c[3] = {tot[0] / I.n_nodes, tot[1] / I.n_nodes, tot[2] / I.n_nodes};
+        const double *S = tot + 3;
+        o[0] = c[0];
+        o[1] = c[1];
+        o[2] = c[2];
+        o[3] = S[0];
+        o[4] = S[1];
+        o[5] = S[2];
+        o[6] = tot[6] - (c[1] * S[2] - c[2] * S[1]);
+        o[7] = tot[7] - (c[2] * S[0] - c[0] * S[2]);
+        o[8] = tot[8] - (c[0] * S[1] - c[1] * S[0]);
+        o[9] = tot[9];
+        o[10] = tot[10];
+        o[11] = tot[11];
+    }
 }
 
 // Block per box: h^3 * sum of the values added by the last spread, from the
