@@ -32,7 +32,7 @@ struct ifem_ctx_s {
     cudaEvent_t ev[6] = {};
     int ev_ok = 0;
     int ev_recorded = 0;
-    int acc64 = 1;
+    int acc64 = 0;
 };
 
 struct ifem_tmpl_s {
@@ -153,10 +153,10 @@ extern "C" int ifem_ctx_create(const ifem_config *cfg, ifem_ctx *out)
     if (!(ctx->cfg.mls_support > 0.0))
         ctx->cfg.mls_support = std::sqrt(3.0);
     ctx->tile = cfg->tile ? cfg->tile : 8;
-    // FP32 spread accumulator width (tuning knob): IFEM_SPREAD_ACC=32 selects
-    // 32-bit fixed point, anything else 64-bit
+    // FP32 spread accumulator width (tuning knob): IFEM_SPREAD_ACC=64 selects
+    // 64-bit fixed point (slower shared-memory atomics), anything else 32-bit
     if (const char *acc = std::getenv("IFEM_SPREAD_ACC"))
-        ctx->acc64 = std::string(acc) == "32" ? 0 : 1;
+        ctx->acc64 = std::string(acc) == "64" ? 1 : 0;
     if (cudaSetDevice(cfg->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, cfg->device) != cudaSuccess ||
         cudaMalloc((void **)&ctx->d_status, sizeof(unsigned long long) * kStatusWords) != cudaSuccess ||

@@ -129,16 +129,13 @@ cudaError_t interp_impl(const TransferArgs &a)
     if (b.n_inst == 0 || b.N == 0)
         return cudaSuccess;
     if constexpr (std::is_same<real, float>::value) {
-        const int E = a.g.max_edge + 4;
-        size_t sm = sizeof(float) * 3 * (size_t)E * E * E;
-        cudaMemsetAsync(a.w.counters + 3, 0, sizeof(int), a.stream);
-        auto kern = a.kernel == 0 ? interp_tile_kernel<0> : interp_tile_kernel<1>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        int occ = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, sm);
-        occ = occ < 1 ? 1 : occ;
-        kern<<<a.n_sm * occ, 256, sm, a.stream>>>(b, a.g, a.w, (const float *)a.u, (const float *)a.x, (float *)a.v,
-                                                  (float)a.support);
+        unsigned grid = (unsigned)((3 * b.N + 255) / 256);
+        if (a.kernel == 0)
+            interp_direct_kernel<0><<<grid, 256, 0, a.stream>>>(b, a.g, a.w, (const float *)a.u, (const float *)a.x,
+                                                               (float *)a.v, (float)a.support);
+        else
+            interp_direct_kernel<1><<<grid, 256, 0, a.stream>>>(b, a.g, a.w, (const float *)a.u, (const float *)a.x,
+                                                               (float *)a.v, (float)a.support);
     } else {
         unsigned grid = (unsigned)((b.N + 255) / 256);
         if (a.kernel == 0)

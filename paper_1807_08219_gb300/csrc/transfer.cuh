@@ -324,6 +324,24 @@ struct FixedPoint<long long> {
     __device__ static __forceinline__ long long conv(float v) { return __float2ll_rn(v); }
 };
 
+// The four Peskin weights of one axis share one square root: with
+// r = s - floor(s) in [0, 1) and q = sqrt(1 + 4r - 4r^2),
+//   phi(1 + r) = (3 - 2r - q)/8, phi(r) = (3 - 2r + q)/8,
+//   phi(1 - r) = (1 + 2r + q)/8, phi(2 - r) = (1 + 2r - q)/8
+// (the radicands of both branches of phi reduce to the same 1 + 4r - 4r^2).
+// Used by the FP32 kernels; the FP64 kernels evaluate phi point by point.
+__device__ __forceinline__ int peskin_axis_fast(float s, float ph[4])
+{
+    const float fl = floorf(s);
+    const float r = s - fl;
+    const float q = sqrtf(fmaxf(1.f + 4.f * r - 4.f * r * r, 0.f));
+    ph[0] = (3.f - 2.f * r - q) * 0.125f;
+    ph[1] = (3.f - 2.f * r + q) * 0.125f;
+    ph[2] = (1.f + 2.f * r + q) * 0.125f;
+    ph[3] = (1.f + 2.f * r - q) * 0.125f;
+    return (int)fl - 1;
+}
+
 __device__ __forceinline__ void acc_add(int *p, int v) { atomicAdd(p, v); }
 // two's-complement addition through the unsigned 64-bit atomic
 __device__ __forceinline__ void acc_add(long long *p, long long v)
@@ -422,38 +440,48 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
             Acc *accd = acc + d * vol;
             if constexpr (KER == 0) {
                 float ph[3][4];
-                int loc[3][4];
+                int lx[4], row[16];
+                unsigned okx = 0, ok = 0;
+                int ly[4], lz[4];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     int I0;
                     float s = LatCoord<float>::get(I, B, a, x[a * N + node], mac_off(d, a), I0);
-                    int i0 = (int)floorf(s) - 1;
-#pragma unroll
-                    for (int m = 0; m < 4; ++m)
-                        ph[a][m] = phi4<float>(s - (float)(i0 + m));
+                    int i0 = peskin_axis_fast(s, ph[a]);
                     int base = wrap_near(I0 + i0, n);
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
                         int idx = base + m;
                         idx -= idx >= n ? n : 0;
-                        loc[a][m] = idx - ti.start[a];
+                        int l = idx - ti.start[a];
+                        if (a == 0) lx[m] = l;
+                        else if (a == 1) ly[m] = l;
+                        else lz[m] = l;
                     }
                 }
 #pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    okx |= ((unsigned)lx[m] < (unsigned)ex) << m;
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+#pragma unroll
+                    for (int bb = 0; bb < 4; ++bb) {
+                        ok |= (((unsigned)lz[c] < (unsigned)ez) && ((unsigned)ly[bb] < (unsigned)ey)) << (4 * c + bb);
+                        row[4 * c + bb] = (lz[c] * ey + ly[bb]) * ex;
+                    }
+#pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    if ((unsigned)loc[2][c] >= (unsigned)ez)
-                        continue;
                     const float wz = ph[2][c] * gq;
 #pragma unroll
                     for (int bb = 0; bb < 4; ++bb) {
-                        if ((unsigned)loc[1][bb] >= (unsigned)ey)
+                        if (!((ok >> (4 * c + bb)) & 1u))
                             continue;
                         const float wyz = ph[1][bb] * wz;
-                        Acc *row = accd + (loc[2][c] * ey + loc[1][bb]) * ex;
+                        Acc *rp = accd + row[4 * c + bb];
 #pragma unroll
                         for (int a = 0; a < 4; ++a)
-                            if ((unsigned)loc[0][a] < (unsigned)ex)
-                                acc_add(row + loc[0][a], FixedPoint<Acc>::conv(ph[0][a] * wyz));
+                            if ((okx >> a) & 1u)
+                                acc_add(rp + lx[a], FixedPoint<Acc>::conv(ph[0][a] * wyz));
                     }
                 }
             } else {
@@ -542,119 +570,88 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
     }
 }
 
-// ------------------------------------------------------- interp, FP32 fast
-// One CTA per tile with own nodes (tiles from a global counter): the tile's
-// velocity footprint (tile + 2 cells of halo per side, three lattices) is
-// staged in shared memory with coalesced row loads, then every (node,
-// lattice) unit gathers its stencil from shared memory:
-// v = sum_z phi_z sum_y phi_y sum_x phi_x u.
+// ------------------------------------------------- interp, FP32 direct
+// Thread per (node, lattice) unit over the nodes in tile order (spatial
+// locality for the L1/L2-cached gathers): v = sum_z phi_z sum_y phi_y
+// sum_x phi_x u, one square root per axis, 32-bit row offsets.
 template <int KER>
-__global__ void __launch_bounds__(256) interp_tile_kernel(DevBatch b, DevGrid g, DevWork w,
-                                                          const float *__restrict__ u,
-                                                          const float *__restrict__ x, float *__restrict__ v,
-                                                          float support)
+__global__ void __launch_bounds__(256) interp_direct_kernel(DevBatch b, DevGrid g, DevWork w,
+                                                            const float *__restrict__ u,
+                                                            const float *__restrict__ x, float *__restrict__ v,
+                                                            float support)
 {
-    extern __shared__ __align__(16) float us[];
-    __shared__ int s_tile;
+    const int total = w.counters[5];
+    const long long unit = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (unit >= 3LL * total)
+        return;
+    const int d = (int)(unit / total);
+    const int node = w.own_nodes[unit - (long long)d * total];
+    const InstDev I = b.inst[b.node_inst[node]];
+    const BoxDev B = g.boxes[I.box];
     const long long N = b.N;
-    const int n_tiles = w.counters[1];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (;;) {
-        if (threadIdx.x == 0)
-            s_tile = atomicAdd(&w.counters[3], 1);
-        __syncthreads();
-        const int it = s_tile;
-        if (it >= n_tiles)
-            break;
-        const int tile = w.own_active[it];
-        const TileInfo ti = decode_tile(g, tile);
-        const BoxDev B = g.boxes[ti.box];
-        const int n = B.n;
-        const int fx = ti.edge[0] + 4, fy = ti.edge[1] + 4, fz = ti.edge[2] + 4;
-        const int fvol = fx * fy * fz;
-        const long long n3 = (long long)n * n * n;
-        // stage: rows (d, z, y) over warps, x over lanes
-        for (int r = wid; r < 3 * fy * fz; r += nw) {
-            const int d = r / (fy * fz);
-            const int rem = r - d * fy * fz;
-            const int lz = rem / fy, ly = rem - lz * fy;
-            const int gz = wrap_near(ti.start[2] - 2 + lz, n), gy = wrap_near(ti.start[1] - 2 + ly, n);
-            const float *row = u + B.grid_off + d * n3 + ((long long)gz * n + gy) * n;
-            float *dst = us + d * fvol + (lz * fy + ly) * fx;
-            for (int lx = lane; lx < fx; lx += 32)
-                dst[lx] = __ldg(row + wrap_near(ti.start[0] - 2 + lx, n));
-        }
-        __syncthreads();
-        const int beg = w.own_off[tile], cnt = w.own_off[tile + 1] - beg;
-        for (int q = threadIdx.x; q < 3 * cnt; q += blockDim.x) {
-            const int d = q / cnt;
-            const int node = w.own_nodes[beg + q - d * cnt];
-            const InstDev I = b.inst[b.node_inst[node]];
-            const float *ud = us + d * fvol;
-            float out = 0.f;
-            if constexpr (KER == 0) {
-                float ph[3][4];
-                int l0[3];
+    const int n = B.n;
+    const float *ud = u + B.grid_off + (long long)d * n * n * n;
+    float out = 0.f;
+    if constexpr (KER == 0) {
+        float ph[3][4];
+        int ix[4], iy[4], iz[4];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    int I0;
-                    float s = LatCoord<float>::get(I, B, a, x[a * N + node], mac_off(d, a), I0);
-                    int i0 = (int)floorf(s) - 1;
+        for (int a = 0; a < 3; ++a) {
+            int I0;
+            float s = LatCoord<float>::get(I, B, a, x[a * N + node], mac_off(d, a), I0);
+            int base = wrap_near(I0 + peskin_axis_fast(s, ph[a]), n);
 #pragma unroll
-                    for (int m = 0; m < 4; ++m)
-                        ph[a][m] = phi4<float>(s - (float)(i0 + m));
-                    int l = wrap_near(I0 + i0, n) - (ti.start[a] - 2);
-                    l += l < 0 ? n : 0;
-                    l -= l >= n ? n : 0;
-                    l0[a] = l;
-                }
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    float accz = 0.f;
-#pragma unroll
-                    for (int bb = 0; bb < 4; ++bb) {
-                        const float *row = ud + ((l0[2] + c) * fy + (l0[1] + bb)) * fx + l0[0];
-                        float accy = ph[0][0] * row[0];
-#pragma unroll
-                        for (int a = 1; a < 4; ++a)
-                            accy += ph[0][a] * row[a];
-                        accz += ph[1][bb] * accy;
-                    }
-                    out += ph[2][c] * accz;
-                }
-            } else {
-                float s[3];
-                int I0[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    s[a] = LatCoord<float>::get(I, B, a, x[a * N + node], mac_off(d, a), I0[a]);
-                int base[3];
-                float wt[27];
-                if (!mls_weights<float>(s, support, base, wt)) {
-                    status_add(w.status, ST_DOMAIN, 1);
-                } else {
-                    int l0[3];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        int l = wrap_near(I0[a] + base[a], n) - (ti.start[a] - 2);
-                        l += l < 0 ? n : 0;
-                        l -= l >= n ? n : 0;
-                        l0[a] = l;
-                    }
-                    int J = 0;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-#pragma unroll
-                        for (int bb = 0; bb < 3; ++bb)
-#pragma unroll
-                            for (int a = 0; a < 3; ++a, ++J)
-                                out += wt[J] * ud[((l0[2] + c) * fy + (l0[1] + bb)) * fx + l0[0] + a];
-                }
+            for (int m = 0; m < 4; ++m) {
+                int idx = base + m;
+                idx -= idx >= n ? n : 0;
+                if (a == 0) ix[m] = idx;
+                else if (a == 1) iy[m] = idx;
+                else iz[m] = idx;
             }
-            v[d * N + node] = out;
         }
-        // the next iteration's first barrier orders these reads before us is rewritten
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float accz = 0.f;
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb) {
+                const float *row = ud + (iz[c] * n + iy[bb]) * n;
+                float accy = ph[0][0] * __ldg(row + ix[0]);
+#pragma unroll
+                for (int a = 1; a < 4; ++a)
+                    accy += ph[0][a] * __ldg(row + ix[a]);
+                accz += ph[1][bb] * accy;
+            }
+            out += ph[2][c] * accz;
+        }
+    } else {
+        float s[3];
+        int I0[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            s[a] = LatCoord<float>::get(I, B, a, x[a * N + node], mac_off(d, a), I0[a]);
+        int base[3];
+        float wt[27];
+        if (!mls_weights<float>(s, support, base, wt)) {
+            status_add(w.status, ST_DOMAIN, 1);
+        } else {
+            int ix[3], iy[3], iz[3];
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                ix[m] = wrap_near(I0[0] + base[0] + m, n);
+                iy[m] = wrap_near(I0[1] + base[1] + m, n);
+                iz[m] = wrap_near(I0[2] + base[2] + m, n);
+            }
+            int J = 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a, ++J)
+                        out += wt[J] * __ldg(ud + (iz[c] * n + iy[bb]) * n + ix[a]);
+        }
     }
+    v[d * N + node] = out;
 }
 
 // ---------------------------------------------- spread, FP64 deterministic
