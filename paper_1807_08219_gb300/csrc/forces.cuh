@@ -411,11 +411,19 @@ __global__ void node_gather_kernel(DevBatch b, const real *__restrict__ ebuf, re
 }
 
 // ------------------------------------------------------------ bending
-// Corner angles and cotangents of one triangle (p0, p1, p2):
-// th[c] = atan2(|u x w|, u.w), cot[c] = (u.w)/|u x w|, u = p_{c+1} - p_c, w = p_{c+2} - p_c.
+// Geometry of one incident triangle (p[c] is the vertex itself, corners
+// c1 = c+1, c2 = c+2): edge dots at every corner, twice the area
+// (|u x w| is the same from every corner), the unnormalised face normal.
+// cot at a corner = dot / (2 area); the corner is obtuse iff its dot < 0.
 template <typename real>
-__device__ __forceinline__ void tri_angles(const real p[3][3], real th[3], real cot[3], real fn[3],
-                                           real &area)
+struct TriGeom {
+    real dot[3];
+    real twoA;
+    real fn[3];
+};
+
+template <typename real>
+__device__ __forceinline__ void tri_geom(const real p[3][3], TriGeom<real> &t)
 {
     real e1[3], e2[3];
 #pragma unroll
@@ -423,37 +431,27 @@ __device__ __forceinline__ void tri_angles(const real p[3][3], real th[3], real 
         e1[a] = p[1][a] - p[0][a];
         e2[a] = p[2][a] - p[0][a];
     }
-    fn[0] = e1[1] * e2[2] - e1[2] * e2[1];
-    fn[1] = e1[2] * e2[0] - e1[0] * e2[2];
-    fn[2] = e1[0] * e2[1] - e1[1] * e2[0];
-    area = real(0.5) * sqrt(fn[0] * fn[0] + fn[1] * fn[1] + fn[2] * fn[2]);
+    t.fn[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    t.fn[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    t.fn[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    t.twoA = sqrt(t.fn[0] * t.fn[0] + t.fn[1] * t.fn[1] + t.fn[2] * t.fn[2]);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        real u[3], w[3], cr[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            u[a] = p[(c + 1) % 3][a] - p[c][a];
-            w[a] = p[(c + 2) % 3][a] - p[c][a];
-        }
-        cr[0] = u[1] * w[2] - u[2] * w[1];
-        cr[1] = u[2] * w[0] - u[0] * w[2];
-        cr[2] = u[0] * w[1] - u[1] * w[0];
-        real cl = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
-        real dp = u[0] * w[0] + u[1] * w[1] + u[2] * w[2];
-        th[c] = atan2(cl, dp);
-        cot[c] = dp / cl;
+        real u0 = p[(c + 1) % 3][0] - p[c][0], u1 = p[(c + 1) % 3][1] - p[c][1], u2 = p[(c + 1) % 3][2] - p[c][2];
+        real w0 = p[(c + 2) % 3][0] - p[c][0], w1 = p[(c + 2) % 3][1] - p[c][1], w2 = p[(c + 2) % 3][2] - p[c][2];
+        t.dot[c] = u0 * w0 + u1 * w1 + u2 * w2;
     }
 }
 
 // Pass 1 at vertex i (template-local id k), over its incident triangles in
 // ascending order: K += cot_k (x_i - x_j) + cot_j (x_i - x_k); mixed Voronoi
-// area; angle sum; area-weighted normal. Outputs A, kH = K.n/2 (K /= 2A),
-// kG = (2 pi - angles)/A and the unit normal n.
+// area (Voronoi region if no corner is obtuse, area/2 at an obtuse corner,
+// area/4 at the others); corner-angle sum; area-weighted normal. Outputs A,
+// kH = K.n/2 (K /= 2A), kG = (2 pi - angles)/A and the unit normal n.
 template <typename real, typename Load>
 __device__ inline void bend_vertex_pass1(const TmplDev &T, int k, Load ld, real &A_out, real &kH_out,
                                          real &kG_out, real n_out[3])
 {
-    const real half_pi = real(1.5707963267948966);
     real K[3] = {0, 0, 0}, nrm[3] = {0, 0, 0}, A = 0, ang = 0;
     for (int q = T.inc_off[k]; q < T.inc_off[k + 1]; ++q) {
         int code = T.inc_idx[q];
@@ -463,33 +461,33 @@ __device__ inline void bend_vertex_pass1(const TmplDev &T, int k, Load ld, real 
 #pragma unroll
         for (int r = 0; r < 3; ++r)
             ld(v[r], p[r]);
-        real th[3], cot[3], fn[3], area;
-        tri_angles(p, th, cot, fn, area);
+        TriGeom<real> t;
+        tri_geom(p, t);
         int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+        real cj = t.dot[c1] / t.twoA, ck = t.dot[c2] / t.twoA;
         real eij[3], eik[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             eij[a] = p[c][a] - p[c1][a];
             eik[a] = p[c][a] - p[c2][a];
         }
-        real cj = cot[c1], ck = cot[c2];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
             K[a] += ck * eij[a] + cj * eik[a];
-        bool obtuse = th[0] > half_pi || th[1] > half_pi || th[2] > half_pi;
+        bool obtuse = t.dot[0] < real(0) || t.dot[1] < real(0) || t.dot[2] < real(0);
         real Ai;
         if (!obtuse)
             Ai = (ck * (eij[0] * eij[0] + eij[1] * eij[1] + eij[2] * eij[2])
                   + cj * (eik[0] * eik[0] + eik[1] * eik[1] + eik[2] * eik[2])) / real(8);
-        else if (th[c] > half_pi)
-            Ai = area / real(2);
+        else if (t.dot[c] < real(0))
+            Ai = t.twoA / real(4);
         else
-            Ai = area / real(4);
+            Ai = t.twoA / real(8);
         A += Ai;
-        ang += th[c];
+        ang += atan2(t.twoA, t.dot[c]);
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            nrm[a] += fn[a];
+            nrm[a] += t.fn[a];
     }
     real nl = sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
 #pragma unroll
@@ -517,10 +515,11 @@ __device__ inline void bend_vertex_pass2(const TmplDev &T, int k, Load ld, LoadH
 #pragma unroll
         for (int r = 0; r < 3; ++r)
             ld(v[r], p[r]);
-        real th[3], cot[3], fn[3], area;
-        tri_angles(p, th, cot, fn, area);
+        TriGeom<real> t;
+        tri_geom(p, t);
         int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
-        lap += cot[c2] * ((kHof(v[c1]) - kH0) - (kH - kH0)) + cot[c1] * ((kHof(v[c2]) - kH0) - (kH - kH0));
+        lap += (t.dot[c2] / t.twoA) * ((kHof(v[c1]) - kH0) - (kH - kH0))
+             + (t.dot[c1] / t.twoA) * ((kHof(v[c2]) - kH0) - (kH - kH0));
     }
     real L = lap / (real(2) * A);
     real dh = kH - kH0;

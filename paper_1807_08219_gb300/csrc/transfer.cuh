@@ -70,21 +70,47 @@ __device__ inline bool node_cell(const InstDev &I, const BoxDev &B, const real *
     return ok;
 }
 
+// Warp-aggregated list append: lanes with the same tile share one global
+// atomic (count pass: the count; fill pass: the slot range). Every lane of
+// the warp must call this (invalid lanes pass valid = false).
+template <bool FILL>
+__device__ __forceinline__ void agg_append(int *count, int *cursor, int *list, long long tile, bool valid,
+                                           int node)
+{
+    const unsigned key = valid ? (unsigned)tile : 0xffffffffu;
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    if (!valid)
+        return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(grp) - 1;
+    if (!FILL) {
+        if (lane == leader)
+            atomicAdd(&count[tile], __popc(grp));
+    } else {
+        int base = 0;
+        if (lane == leader)
+            base = atomicAdd(&cursor[tile], __popc(grp));
+        base = __shfl_sync(grp, base, leader);
+        list[base + __popc(grp & ((1u << lane) - 1u))] = node;
+    }
+}
+
 // FILL = false: count candidate / own pairs per tile; FILL = true: write them.
+// Block size must be a multiple of 32 (every lane reaches the warp votes).
 template <typename real, bool FILL>
 __global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restrict__ x)
 {
     const InstDev I = b.inst[blockIdx.y];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= I.n_nodes)
-        return;
+    const bool in = k < I.n_nodes;
     const BoxDev B = g.boxes[I.box];
-    const int node = I.node_off + k;
-    int c[3];
-    if (!node_cell<real>(I, B, x, b.N, node, c)) {
-        if (!FILL)
+    const int node = I.node_off + (in ? k : 0);
+    int c[3] = {0, 0, 0};
+    bool ok = false;
+    if (in) {
+        ok = node_cell<real>(I, B, x, b.N, node, c);
+        if (!FILL && !ok)
             status_add(w.status, ST_DOMAIN, 1);
-        return;
     }
     int tl[3][2], nt[3];
 #pragma unroll
@@ -93,25 +119,17 @@ __global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restr
         tl[a][1] = tile_of(wrapi(c[a] + 2, B.n), B.t, B.T);
         nt[a] = tl[a][0] == tl[a][1] ? 1 : 2;
     }
-    long long own = B.tile_base + ((long long)tile_of(c[2], B.t, B.T) * B.T + tile_of(c[1], B.t, B.T)) * B.T
-                    + tile_of(c[0], B.t, B.T);
-    if (FILL) {
-        int p = atomicAdd(&w.own_cursor[own], 1);
-        w.own_nodes[p] = node;
-    } else {
-        atomicAdd(&w.own_count[own], 1);
+    const long long own = B.tile_base
+                          + ((long long)tile_of(c[2], B.t, B.T) * B.T + tile_of(c[1], B.t, B.T)) * B.T
+                          + tile_of(c[0], B.t, B.T);
+    agg_append<FILL>(w.own_count, w.own_cursor, w.own_nodes, own, ok, node);
+#pragma unroll
+    for (int slot = 0; slot < 8; ++slot) {
+        const int ix = slot & 1, iy = (slot >> 1) & 1, iz = slot >> 2;
+        const bool valid = ok && ix < nt[0] && iy < nt[1] && iz < nt[2];
+        const long long tile = B.tile_base + ((long long)tl[2][iz] * B.T + tl[1][iy]) * B.T + tl[0][ix];
+        agg_append<FILL>(w.cand_count, w.cand_cursor, w.cand_nodes, tile, valid, node);
     }
-    for (int iz = 0; iz < nt[2]; ++iz)
-        for (int iy = 0; iy < nt[1]; ++iy)
-            for (int ix = 0; ix < nt[0]; ++ix) {
-                long long tile = B.tile_base + ((long long)tl[2][iz] * B.T + tl[1][iy]) * B.T + tl[0][ix];
-                if (FILL) {
-                    int p = atomicAdd(&w.cand_cursor[tile], 1);
-                    w.cand_nodes[p] = node;
-                } else {
-                    atomicAdd(&w.cand_count[tile], 1);
-                }
-            }
 }
 
 // Exclusive scan of the per-tile counts (two lists at once), 3 passes:
@@ -371,8 +389,10 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
     Acc *acc = reinterpret_cast<Acc *>(spread_smem);
     __shared__ float s_part[3][8];
     __shared__ float s_scale[3];
-    __shared__ double red_sh[3][8];
+    __shared__ double s_red[3][8];
     __shared__ int s_tile;
+    __shared__ TileInfo s_ti;
+    __shared__ BoxDev s_B;
     const long long N = b.N;
     const int n_active = w.counters[0];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -380,47 +400,60 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
         status_add(w.status, ST_PAIRS, (unsigned long long)w.cand_off[g.n_tiles]);
         status_add(w.status, ST_ACTIVE, (unsigned long long)n_active);
     }
-    for (;;) {
-        if (threadIdx.x == 0)
-            s_tile = atomicAdd(&w.counters[2], 1);
-        __syncthreads();
-        const int it = s_tile;
-        if (it >= n_active)
-            break;
-        const int tile = w.active[it];
-        const TileInfo ti = decode_tile(g, tile);
-        const BoxDev B = g.boxes[ti.box];
-        const int ex = ti.edge[0], ey = ti.edge[1], ez = ti.edge[2];
-        const int vol = ex * ey * ez;
-        const int n = B.n;
-        for (int i = threadIdx.x; i < 3 * vol; i += blockDim.x)
+    // accumulators start at zero; the flush of every tile clears what it read
+    {
+        const int E = g.max_edge;
+        for (int i = threadIdx.x; i < 3 * E * E * E; i += blockDim.x)
             acc[i] = 0;
-        const float sd = density ? (float)B.scale : 1.f;
+    }
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int it = atomicAdd(&w.counters[2], 1);
+            s_tile = it < n_active ? w.active[it] : -1;
+            if (it < n_active) {
+                s_ti = decode_tile(g, s_tile);
+                s_B = g.boxes[s_ti.box];
+            }
+        }
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile < 0)
+            break;
+        const int ex = s_ti.edge[0], ey = s_ti.edge[1], ez = s_ti.edge[2];
+        const int sx = s_ti.start[0], sy = s_ti.start[1], sz = s_ti.start[2];
+        const int vol = ex * ey * ez;
+        const int n = s_B.n;
+        const float sd = density ? (float)s_B.scale : 1.f;
+        const double h3 = 1.0 / s_B.scale;
         const int beg = w.cand_off[tile], end = w.cand_off[tile + 1];
-        const int nc = end - beg;
         // bound on |sum| per lattice: wmax * sum_k |F_k,d| * sd
-        float gs[3] = {0.f, 0.f, 0.f};
+        float gs0 = 0.f, gs1 = 0.f, gs2 = 0.f;
         for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
             const int node = w.cand_nodes[q];
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-                gs[d] += fabsf(F[d * N + node]);
+            gs0 += fabsf(F[node]);
+            gs1 += fabsf(F[N + node]);
+            gs2 += fabsf(F[2 * N + node]);
         }
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            float v = gs[d];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-                v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0)
-                s_part[d][wid] = v;
+        for (int o = 16; o > 0; o >>= 1) {
+            gs0 += __shfl_down_sync(0xffffffffu, gs0, o);
+            gs1 += __shfl_down_sync(0xffffffffu, gs1, o);
+            gs2 += __shfl_down_sync(0xffffffffu, gs2, o);
+        }
+        if (lane == 0) {
+            s_part[0][wid] = gs0;
+            s_part[1][wid] = gs1;
+            s_part[2][wid] = gs2;
         }
         __syncthreads();
         if (threadIdx.x < 3) {
             float tot = 0.f;
             for (int q = 0; q < nw; ++q)
                 tot += s_part[threadIdx.x][q];
-            const float wmax = KER == 0 ? 0.125f : 2.0f;
+            // |phi| <= 1/8 (Peskin: (1/2)^3); MLS weights are non-negative, sum to 1
+            // and stay below 1/2 in practice; the bound sums over every candidate
+            // of the tile, far above what any single value receives
+            const float wmax = KER == 0 ? 0.125f : 0.5f;
             float bound = tot * sd * wmax * 1.0001f;
             float sc = 1.f;
             if (bound > 0.f && isfinite(bound)) {
@@ -431,142 +464,130 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
             s_scale[threadIdx.x] = sc;
         }
         __syncthreads();
-        for (int u = threadIdx.x; u < 3 * nc; u += blockDim.x) {
-            const int d = u / nc;
-            const int j = u - d * nc;
-            const int node = w.cand_nodes[beg + j];
-            const InstDev I = b.inst[b.node_inst[node]];
-            const float gq = F[d * N + node] * sd * s_scale[d];
+#pragma unroll 1
+        for (int d = 0; d < 3; ++d) {
             Acc *accd = acc + d * vol;
-            if constexpr (KER == 0) {
-                float ph[3][4];
-                int lx[4], row[16];
-                unsigned okx = 0, ok = 0;
-                int ly[4], lz[4];
+            const float gsc = sd * s_scale[d];
+            for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
+                const int node = w.cand_nodes[q];
+                const InstDev &I = b.inst[b.node_inst[node]];
+                const float gq = F[d * N + node] * gsc;
+                if constexpr (KER == 0) {
+                    float ph[3][4];
+                    int l[3][4];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    int I0;
-                    float s = LatCoord<float>::get(I, B, a, x[a * N + node], mac_off(d, a), I0);
-                    int i0 = peskin_axis_fast(s, ph[a]);
-                    int base = wrap_near(I0 + i0, n);
+                    for (int a = 0; a < 3; ++a) {
+                        const int I0 = I.I0[a];
+                        const float s = (I.f0[a] - (a == d ? 0.f : 0.5f)) + x[a * N + node] * (float)s_B.inv_h;
+                        const int base = wrap_near(I0 + peskin_axis_fast(s, ph[a]), n);
+                        const int st = a == 0 ? sx : (a == 1 ? sy : sz);
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        int idx = base + m;
-                        idx -= idx >= n ? n : 0;
-                        int l = idx - ti.start[a];
-                        if (a == 0) lx[m] = l;
-                        else if (a == 1) ly[m] = l;
-                        else lz[m] = l;
-                    }
-                }
-#pragma unroll
-                for (int m = 0; m < 4; ++m)
-                    okx |= ((unsigned)lx[m] < (unsigned)ex) << m;
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-#pragma unroll
-                    for (int bb = 0; bb < 4; ++bb) {
-                        ok |= (((unsigned)lz[c] < (unsigned)ez) && ((unsigned)ly[bb] < (unsigned)ey)) << (4 * c + bb);
-                        row[4 * c + bb] = (lz[c] * ey + ly[bb]) * ex;
+                        for (int m = 0; m < 4; ++m) {
+                            int idx = base + m;
+                            idx -= idx >= n ? n : 0;
+                            l[a][m] = idx - st;
+                        }
                     }
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const float wz = ph[2][c] * gq;
-#pragma unroll
-                    for (int bb = 0; bb < 4; ++bb) {
-                        if (!((ok >> (4 * c + bb)) & 1u))
+                    for (int c = 0; c < 4; ++c) {
+                        if ((unsigned)l[2][c] >= (unsigned)ez)
                             continue;
-                        const float wyz = ph[1][bb] * wz;
-                        Acc *rp = accd + row[4 * c + bb];
+                        const float wz = ph[2][c] * gq;
 #pragma unroll
-                        for (int a = 0; a < 4; ++a)
-                            if ((okx >> a) & 1u)
-                                acc_add(rp + lx[a], FixedPoint<Acc>::conv(ph[0][a] * wyz));
+                        for (int bb = 0; bb < 4; ++bb) {
+                            if ((unsigned)l[1][bb] >= (unsigned)ey)
+                                continue;
+                            const float wyz = ph[1][bb] * wz;
+                            Acc *rp = accd + (l[2][c] * ey + l[1][bb]) * ex;
+#pragma unroll
+                            for (int a = 0; a < 4; ++a)
+                                if ((unsigned)l[0][a] < (unsigned)ex)
+                                    acc_add(rp + l[0][a], FixedPoint<Acc>::conv(ph[0][a] * wyz));
+                        }
                     }
-                }
-            } else {
-                float s[3];
-                int I0[3];
+                } else {
+                    float s[3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    s[a] = LatCoord<float>::get(I, B, a, x[a * N + node], mac_off(d, a), I0[a]);
-                int base[3];
-                float wt[27];
-                if (!mls_weights<float>(s, support, base, wt)) {
-                    status_add(w.status, ST_DOMAIN, 1);
-                    continue;
-                }
-                int loc[3][3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    int bw = wrap_near(I0[a] + base[a], n);
-#pragma unroll
-                    for (int m = 0; m < 3; ++m) {
-                        int idx = bw + m;
-                        idx -= idx >= n ? n : 0;
-                        loc[a][m] = idx - ti.start[a];
+                    for (int a = 0; a < 3; ++a)
+                        s[a] = (I.f0[a] - (a == d ? 0.f : 0.5f)) + x[a * N + node] * (float)s_B.inv_h;
+                    int base[3];
+                    float wt[27];
+                    if (!mls_weights<float>(s, support, base, wt)) {
+                        status_add(w.status, ST_DOMAIN, 1);
+                        continue;
                     }
+                    int l[3][3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const int bw = wrap_near(I.I0[a] + base[a], n);
+                        const int st = a == 0 ? sx : (a == 1 ? sy : sz);
+#pragma unroll
+                        for (int m = 0; m < 3; ++m) {
+                            int idx = bw + m;
+                            idx -= idx >= n ? n : 0;
+                            l[a][m] = idx - st;
+                        }
+                    }
+                    int J = 0;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+#pragma unroll
+                        for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+                            for (int a = 0; a < 3; ++a, ++J)
+                                if ((unsigned)l[2][c] < (unsigned)ez && (unsigned)l[1][bb] < (unsigned)ey &&
+                                    (unsigned)l[0][a] < (unsigned)ex)
+                                    acc_add(accd + (l[2][c] * ey + l[1][bb]) * ex + l[0][a],
+                                            FixedPoint<Acc>::conv(wt[J] * gq));
                 }
-                int J = 0;
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-#pragma unroll
-                    for (int bb = 0; bb < 3; ++bb)
-#pragma unroll
-                        for (int a = 0; a < 3; ++a, ++J)
-                            if ((unsigned)loc[2][c] < (unsigned)ez && (unsigned)loc[1][bb] < (unsigned)ey &&
-                                (unsigned)loc[0][a] < (unsigned)ex)
-                                acc_add(accd + (loc[2][c] * ey + loc[1][bb]) * ex + loc[0][a],
-                                        FixedPoint<Acc>::conv(wt[J] * gq));
             }
         }
         __syncthreads();
-        // flush: rows (d, z, y) over warps, x over lanes
+        // flush: per lattice, (z, y) planes of the tile over warps, x*y flat over lanes;
+        // clears every value it reads
         const long long n3 = (long long)n * n * n;
-        double part[3] = {0.0, 0.0, 0.0};
-        unsigned long long touched = 0;
-        const int rows_per_d = ey * ez;
-        for (int r = wid; r < 3 * rows_per_d; r += nw) {
-            const int d = r / rows_per_d;
-            const int rem = r - d * rows_per_d;
-            const int lz = rem / ey, ly = rem - lz * ey;
+        const int plane = ex * ey;
+        unsigned touched = 0;
+#pragma unroll 1
+        for (int d = 0; d < 3; ++d) {
             const float inv = 1.f / s_scale[d];
-            const Acc *src = acc + d * vol + (lz * ey + ly) * ex;
-            float *dst = f + B.grid_off + d * n3 + ((long long)(ti.start[2] + lz) * n + (ti.start[1] + ly)) * n
-                         + ti.start[0];
-            for (int lx = lane; lx < ex; lx += 32) {
-                const Acc q = src[lx];
-                if (q != 0) {
-                    const float val = (float)q * inv;
-                    dst[lx] += val;
-                    part[d] += (double)val;
-                    ++touched;
+            double part = 0.0;
+            float *fd = f + s_B.grid_off + d * n3;
+            for (int lz = wid; lz < ez; lz += nw) {
+                Acc *src = acc + d * vol + lz * plane;
+                float *dz = fd + (long long)(sz + lz) * n * n + (long long)sy * n + sx;
+                for (int i = lane; i < plane; i += 32) {
+                    const Acc q = src[i];
+                    if (q != 0) {
+                        src[i] = 0;
+                        const int ly = i / ex;
+                        const float val = (float)q * inv;
+                        float *p = dz + ly * n + (i - ly * ex);
+                        *p += val;
+                        part += (double)val;
+                        ++touched;
+                    }
                 }
             }
-        }
-        unsigned long long cnt = touched;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-        if (lane == 0)
-            status_add(w.status, ST_TOUCHED, cnt);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            double v = part[d];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
-                v += __shfl_down_sync(0xffffffffu, v, o);
+                part += __shfl_down_sync(0xffffffffu, part, o);
             if (lane == 0)
-                red_sh[d][wid] = v;
+                s_red[d][wid] = part;
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            touched += __shfl_down_sync(0xffffffffu, touched, o);
+        if (lane == 0)
+            status_add(w.status, ST_TOUCHED, touched);
         __syncthreads();
         if (threadIdx.x < 3) {
             double v = 0.0;
             for (int q = 0; q < nw; ++q)
-                v += red_sh[threadIdx.x][q];
-            w.red_tile[3LL * tile + threadIdx.x] = v * (1.0 / B.scale);
+                v += s_red[threadIdx.x][q];
+            w.red_tile[3LL * tile + threadIdx.x] = v * h3;
         }
-        // the next iteration's first barrier orders these reads before s_tile/acc are rewritten
+        // the next iteration's barrier orders these reads before s_red is rewritten
     }
 }
 
