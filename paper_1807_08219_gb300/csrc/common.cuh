@@ -19,9 +19,9 @@ constexpr int kMaxTileEdge = 20;   // tile edge t + 4 at most (t <= 16)
 constexpr int kScanThreads = 512;  // tile-count scan: threads per block
 constexpr int kScanPer = 4;        // and values per thread
 constexpr int kScanBlock = kScanThreads * kScanPer;
-// FP32 fused force kernel: 12 floats of shared memory per template node
+// FP32 fused force kernel: 7 floats of shared memory per template node
 constexpr int kFusedMaxSmemBytes = 227 * 1024;
-__host__ __device__ inline size_t fused_smem_bytes(int n_nodes) { return (size_t)12 * n_nodes * sizeof(float); }
+__host__ __device__ inline size_t fused_smem_bytes(int n_nodes) { return (size_t)7 * n_nodes * sizeof(float); }
 constexpr int kStatusWords = 8;
 enum StatusWord {
     ST_INVERTED = 0,

@@ -583,11 +583,16 @@ __global__ void bend_pass2_kernel(DevBatch b, const real *__restrict__ x, const 
 // ------------------------------------------------------------ FP32 fused path
 // One CTA per instance: node positions and force accumulators in shared
 // memory, element forces added with shared-memory atomics (order not
-// reproducible), then both bending passes from shared memory, then one
-// coalesced write of F. Shared memory: 3n (x) + 3n (F) + 6n (bending) floats.
-static __global__ void __launch_bounds__(512) forces_fused_f32_kernel(DevBatch b, const float *__restrict__ x,
-                                                               float *__restrict__ F,
-                                                               unsigned long long *status)
+// reproducible), then the two bending passes, then one coalesced write of F.
+// The bending force is split so that only kH is kept between the passes:
+//   pass 1 (vertex i): F_i += 2 kb * 2 (kH - kH0)(kH^2 - kG + kH0 kH) A_i n_i
+//   pass 2 (vertex i): F_i += 2 kb * Lap(kH - kH0) A_i n_i = kb * lap_i * n_i
+// where lap_i = sum_j (cot a_ij + cot b_ij)(kH_j - kH_i) (A_i cancels) and n_i
+// is recomputed from the incident faces in the same order as in pass 1.
+// Shared memory: 3n (x) + 3n (F) + n (kH) floats.
+static __global__ void __launch_bounds__(256) forces_fused_f32_kernel(DevBatch b, const float *__restrict__ x,
+                                                                      float *__restrict__ F,
+                                                                      unsigned long long *status)
 {
     extern __shared__ float sm[];
     const InstDev I = b.inst[blockIdx.x];
@@ -596,7 +601,7 @@ static __global__ void __launch_bounds__(512) forces_fused_f32_kernel(DevBatch b
     const long long N = b.N;
     float *xs = sm;               // [3][nn]
     float *Fs = sm + 3 * nn;      // [3][nn]
-    float *bs = sm + 6 * nn;      // [6][nn]: A, kH, kG, n0, n1, n2
+    float *kHs = sm + 6 * nn;     // [nn]
     for (int k = threadIdx.x; k < nn; k += blockDim.x) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -645,6 +650,7 @@ static __global__ void __launch_bounds__(512) forces_fused_f32_kernel(DevBatch b
         }
     }
     if (T.kind == 0 && T.kb != 0.0) {
+        const float kb = (float)T.kb, kH0 = -0.5f * (float)T.c0;
         auto ld = [&](int v, float p[3]) {
             p[0] = xs[v];
             p[1] = xs[nn + v];
@@ -653,17 +659,37 @@ static __global__ void __launch_bounds__(512) forces_fused_f32_kernel(DevBatch b
         for (int k = threadIdx.x; k < nn; k += blockDim.x) {
             float A, kH, kG, n[3];
             bend_vertex_pass1<float>(T, k, ld, A, kH, kG, n);
-            bs[k] = A; bs[nn + k] = kH; bs[2 * nn + k] = kG;
-            bs[3 * nn + k] = n[0]; bs[4 * nn + k] = n[1]; bs[5 * nn + k] = n[2];
-        }
-        __syncthreads();
-        auto kHof = [&](int v) { return bs[nn + v]; };
-        for (int k = threadIdx.x; k < nn; k += blockDim.x) {
-            float n[3] = {bs[3 * nn + k], bs[4 * nn + k], bs[5 * nn + k]}, Fb[3];
-            bend_vertex_pass2<float>(T, k, ld, kHof, bs[k], bs[nn + k], bs[2 * nn + k], n, Fb);
+            kHs[k] = kH;
+            const float dh = kH - kH0;
+            const float mag = 2.f * kb * (2.f * dh * (kH * kH - kG + kH0 * kH)) * A;
 #pragma unroll
             for (int a = 0; a < 3; ++a)
-                atomicAdd(&Fs[a * nn + k], Fb[a]);
+                atomicAdd(&Fs[a * nn + k], mag * n[a]);
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < nn; k += blockDim.x) {
+            float lap = 0.f, nrm[3] = {0.f, 0.f, 0.f};
+            const float kHk = kHs[k];
+            for (int q = T.inc_off[k]; q < T.inc_off[k + 1]; ++q) {
+                const int code = T.inc_idx[q];
+                const int e = code >> 2, c = code & 3;
+                const int v[3] = {T.elems[3 * e], T.elems[3 * e + 1], T.elems[3 * e + 2]};
+                float p[3][3];
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    ld(v[r], p[r]);
+                TriGeom<float> t;
+                tri_geom(p, t);
+                const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+                lap += (t.dot[c2] / t.twoA) * (kHs[v[c1]] - kHk) + (t.dot[c1] / t.twoA) * (kHs[v[c2]] - kHk);
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    nrm[a] += t.fn[a];
+            }
+            const float s = kb * lap * rsqrtf(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                atomicAdd(&Fs[a * nn + k], s * nrm[a]);
         }
     }
     __syncthreads();
@@ -679,6 +705,5 @@ static __global__ void __launch_bounds__(512) forces_fused_f32_kernel(DevBatch b
     if ((threadIdx.x & 31) == 0)
         status_add(status, ST_INVERTED, tot);
 }
-
 
 }  // namespace ifem

@@ -65,7 +65,13 @@ __device__ inline bool node_cell(const InstDev &I, const BoxDev &B, const real *
         ok = ok && isfinite(xa);
         int I0;
         real s = LatCoord<real>::get(I, B, a, xa, real(0), I0);
-        c[a] = ok ? wrapi((long long)I0 + (long long)floor(s), B.n) : 0;
+        long long ci = (long long)I0 + (long long)floor(s);
+        int cw;
+        if (ci >= 0 && ci < 2LL * B.n)
+            cw = ci >= B.n ? (int)ci - B.n : (int)ci;
+        else
+            cw = wrapi(ci, B.n);
+        c[a] = ok ? cw : 0;
     }
     return ok;
 }
@@ -115,8 +121,11 @@ __global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restr
     int tl[3][2], nt[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        tl[a][0] = tile_of(wrapi(c[a] - 2, B.n), B.t, B.T);
-        tl[a][1] = tile_of(wrapi(c[a] + 2, B.n), B.t, B.T);
+        int lo = c[a] - 2, hi = c[a] + 2;
+        lo += lo < 0 ? B.n : 0;
+        hi -= hi >= B.n ? B.n : 0;
+        tl[a][0] = tile_of(lo, B.t, B.T);
+        tl[a][1] = tile_of(hi, B.t, B.T);
         nt[a] = tl[a][0] == tl[a][1] ? 1 : 2;
     }
     const long long own = B.tile_base
