@@ -590,7 +590,7 @@ __global__ void bend_pass2_kernel(DevBatch b, const real *__restrict__ x, const 
 // where lap_i = sum_j (cot a_ij + cot b_ij)(kH_j - kH_i) (A_i cancels) and n_i
 // is recomputed from the incident faces in the same order as in pass 1.
 // Shared memory: 3n (x) + 3n (F) + n (kH) floats.
-static __global__ void __launch_bounds__(256) forces_fused_f32_kernel(DevBatch b, const float *__restrict__ x,
+static __global__ void __launch_bounds__(512, 2) forces_fused_f32_kernel(DevBatch b, const float *__restrict__ x,
                                                                       float *__restrict__ F,
                                                                       unsigned long long *status)
 {

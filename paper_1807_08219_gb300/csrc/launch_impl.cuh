@@ -29,7 +29,7 @@ cudaError_t forces_impl(const ForcesArgs &a)
         if (!a.hvp && a.scatter == 1 && b.fused_ok) {
         size_t sm = fused_smem_bytes(b.max_nodes);
         cudaFuncSetAttribute(forces_fused_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        forces_fused_f32_kernel<<<b.n_inst, 256, sm, s>>>(b, (const float *)a.x, (float *)a.F, a.w.status);
+        forces_fused_f32_kernel<<<b.n_inst, 512, sm, s>>>(b, (const float *)a.x, (float *)a.F, a.w.status);
         IFEM_LAUNCH_CHECK();
         return cudaSuccess;
         }

@@ -13,6 +13,8 @@
 // contribution that lands in it and writes each touched value once, so no
 // global atomics are needed and no value is written by two CTAs.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace ifem {
@@ -473,48 +475,65 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
             s_scale[threadIdx.x] = sc;
         }
         __syncthreads();
-#pragma unroll 1
-        for (int d = 0; d < 3; ++d) {
-            Acc *accd = acc + d * vol;
-            const float gsc = sd * s_scale[d];
+        if constexpr (KER == 0) {
+            // node units: the three MAC lattices share weights per axis (the
+            // lattice whose component is along the axis uses s, the other two
+            // s - 1/2), so 6 one-dimensional stencils serve all 192 points
+            const float inv_h = (float)s_B.inv_h;
+            const float g0 = sd * s_scale[0], g1 = sd * s_scale[1], g2 = sd * s_scale[2];
             for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
                 const int node = w.cand_nodes[q];
                 const InstDev &I = b.inst[b.node_inst[node]];
-                const float gq = F[d * N + node] * gsc;
-                if constexpr (KER == 0) {
-                    float ph[3][4];
-                    int l[3][4];
+                float ph[2][3][4];   // [shifted][axis][m]
+                int l[2][3][4];
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        const int I0 = I.I0[a];
-                        const float s = (I.f0[a] - (a == d ? 0.f : 0.5f)) + x[a * N + node] * (float)s_B.inv_h;
-                        const int base = wrap_near(I0 + peskin_axis_fast(s, ph[a]), n);
-                        const int st = a == 0 ? sx : (a == 1 ? sy : sz);
+                for (int a = 0; a < 3; ++a) {
+                    const float t = I.f0[a] + x[a * N + node] * inv_h;
+                    const int st = a == 0 ? sx : (a == 1 ? sy : sz);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int base = wrap_near(I.I0[a] + peskin_axis_fast(h ? t - 0.5f : t, ph[h][a]), n);
 #pragma unroll
                         for (int m = 0; m < 4; ++m) {
                             int idx = base + m;
                             idx -= idx >= n ? n : 0;
-                            l[a][m] = idx - st;
+                            l[h][a][m] = idx - st;
                         }
                     }
+                }
+                const float gq[3] = {F[node] * g0, F[N + node] * g1, F[2 * N + node] * g2};
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const int hx = d == 0 ? 0 : 1, hy = d == 1 ? 0 : 1, hz = d == 2 ? 0 : 1;
+                    Acc *accd = acc + d * vol;
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        if ((unsigned)l[2][c] >= (unsigned)ez)
+                        if ((unsigned)l[hz][2][c] >= (unsigned)ez)
                             continue;
-                        const float wz = ph[2][c] * gq;
+                        const float wz = ph[hz][2][c] * gq[d];
 #pragma unroll
                         for (int bb = 0; bb < 4; ++bb) {
-                            if ((unsigned)l[1][bb] >= (unsigned)ey)
+                            if ((unsigned)l[hy][1][bb] >= (unsigned)ey)
                                 continue;
-                            const float wyz = ph[1][bb] * wz;
-                            Acc *rp = accd + (l[2][c] * ey + l[1][bb]) * ex;
+                            const float wyz = ph[hy][1][bb] * wz;
+                            Acc *rp = accd + (l[hz][2][c] * ey + l[hy][1][bb]) * ex;
 #pragma unroll
                             for (int a = 0; a < 4; ++a)
-                                if ((unsigned)l[0][a] < (unsigned)ex)
-                                    acc_add(rp + l[0][a], FixedPoint<Acc>::conv(ph[0][a] * wyz));
+                                if ((unsigned)l[hx][0][a] < (unsigned)ex)
+                                    acc_add(rp + l[hx][0][a], FixedPoint<Acc>::conv(ph[hx][0][a] * wyz));
                         }
                     }
-                } else {
+                }
+            }
+        } else {
+#pragma unroll 1
+        for (int d = 0; d < 3; ++d) {
+            Acc *accd = acc + d * vol;
+            const float gsc = sd * s_scale[d];            for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
+                const int node = w.cand_nodes[q];
+                const InstDev &I = b.inst[b.node_inst[node]];
+                const float gq = F[d * N + node] * gsc;
+                {
                     float s[3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
@@ -550,6 +569,7 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
                                             FixedPoint<Acc>::conv(wt[J] * gq));
                 }
             }
+        }
         }
         __syncthreads();
         // flush: per lattice, (z, y) planes of the tile over warps, x*y flat over lanes;
@@ -1001,8 +1021,32 @@ __device__ inline double block_sum(double v, double *sh)
     return r;
 }
 
-// One pass per instance: FP64 partial sums of x, F, v and x (x) F (about the
-// instance's local origin) per thread, then a fixed-order warp/CTA tree.
+// Per-thread partial sums as unevaluated float pairs (hi + lo, Knuth's
+// TwoSum and the FMA product error): about 44 significant bits, at FP32
+// speed; the FP64 pipe of this GPU is far narrower than its FP32 pipe.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ void df_add(DF &x, float v)
+{
+    const float s = x.hi + v;
+    const float bv = s - x.hi;
+    const float e = (x.hi - (s - bv)) + (v - bv);
+    const float t = x.lo + e;
+    x.hi = s + t;
+    x.lo = t - (x.hi - s);
+}
+__device__ __forceinline__ void df_add_prod(DF &x, float a, float b)
+{
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);
+    df_add(x, p);
+    x.lo += pe;
+}
+
+// One pass per instance: partial sums of x, F, v and x (x) F (about the
+// instance's local origin) per thread -- float pairs for FP32 inputs, FP64
+// for FP64 inputs -- then FP64 in a fixed warp/CTA tree.
 // Torque about the centroid: sum (x - c) x F = sum x x F - c x sum F.
 template <typename real>
 __global__ void __launch_bounds__(256) reduce_inst_kernel(DevBatch b, const real *__restrict__ x,
@@ -1010,26 +1054,55 @@ __global__ void __launch_bounds__(256) reduce_inst_kernel(DevBatch b, const real
                                                           const real *__restrict__ v, double *__restrict__ red)
 {
     __shared__ double sh[12][8];
+    __shared__ double tot[12];
     const InstDev I = b.inst[blockIdx.x];
     const long long N = b.N;
     double p[12];
+    if constexpr (std::is_same<real, float>::value) {
+        DF q[12];
 #pragma unroll
-    for (int q = 0; q < 12; ++q)
-        p[q] = 0.0;
-    for (int k = threadIdx.x; k < I.n_nodes; k += blockDim.x) {
-        const int node = I.node_off + k;
-        double xk[3], Fk[3];
+        for (int i = 0; i < 12; ++i)
+            q[i] = DF{0.f, 0.f};
+        for (int k = threadIdx.x; k < I.n_nodes; k += blockDim.x) {
+            const int node = I.node_off + k;
+            float xk[3], Fk[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            xk[a] = (double)x[a * N + node];
-            Fk[a] = F ? (double)F[a * N + node] : 0.0;
-            p[a] += xk[a];
-            p[3 + a] += Fk[a];
-            p[9 + a] += v ? (double)v[a * N + node] : 0.0;
+            for (int a = 0; a < 3; ++a) {
+                xk[a] = x[a * N + node];
+                Fk[a] = F ? F[a * N + node] : 0.f;
+                df_add(q[a], xk[a]);
+                df_add(q[3 + a], Fk[a]);
+                df_add(q[9 + a], v ? v[a * N + node] : 0.f);
+            }
+            df_add_prod(q[6], xk[1], Fk[2]);
+            df_add_prod(q[6], -xk[2], Fk[1]);
+            df_add_prod(q[7], xk[2], Fk[0]);
+            df_add_prod(q[7], -xk[0], Fk[2]);
+            df_add_prod(q[8], xk[0], Fk[1]);
+            df_add_prod(q[8], -xk[1], Fk[0]);
         }
-        p[6] += xk[1] * Fk[2] - xk[2] * Fk[1];
-        p[7] += xk[2] * Fk[0] - xk[0] * Fk[2];
-        p[8] += xk[0] * Fk[1] - xk[1] * Fk[0];
+#pragma unroll
+        for (int i = 0; i < 12; ++i)
+            p[i] = (double)q[i].hi + (double)q[i].lo;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 12; ++i)
+            p[i] = 0.0;
+        for (int k = threadIdx.x; k < I.n_nodes; k += blockDim.x) {
+            const int node = I.node_off + k;
+            double xk[3], Fk[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                xk[a] = (double)x[a * N + node];
+                Fk[a] = F ? (double)F[a * N + node] : 0.0;
+                p[a] += xk[a];
+                p[3 + a] += Fk[a];
+                p[9 + a] += v ? (double)v[a * N + node] : 0.0;
+            }
+            p[6] += xk[1] * Fk[2] - xk[2] * Fk[1];
+            p[7] += xk[2] * Fk[0] - xk[0] * Fk[2];
+            p[8] += xk[0] * Fk[1] - xk[1] * Fk[0];
+        }
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -1042,7 +1115,6 @@ __global__ void __launch_bounds__(256) reduce_inst_kernel(DevBatch b, const real
             sh[q][wid] = t;
     }
     __syncthreads();
-    __shared__ double tot[12];
     if (threadIdx.x < 12) {
         double t = 0.0;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
