@@ -672,6 +672,8 @@ static int ws_ensure(ifem_ctx ctx, ifem_batch b, ifem_grid g, int tile)
         B.L = g->L[i];
         B.inv_h = (double)B.n / B.L;
         B.scale = B.inv_h * B.inv_h * B.inv_h;
+        B.inv_h_f = (float)B.inv_h;
+        B.scale_f = (float)B.scale;
         nt += (long long)B.T * B.T * B.T;
         for (int j = 0; j < B.T; ++j)
             max_edge = std::max(max_edge, tile_edge(j, B.t, B.T, B.n));

@@ -69,6 +69,8 @@ struct BoxDev {
     double L;
     double inv_h;          // n / L
     double scale;          // (n/L)^3
+    float inv_h_f;         // FP32 copies for the FP32 kernels (no FP64 pipe use)
+    float scale_f;
 };
 
 struct DevBatch {
@@ -267,7 +269,7 @@ struct LatCoord<float> {
     __device__ static inline float get(const InstDev &I, const BoxDev &B, int a, float x, float o, int &I0)
     {
         I0 = I.I0[a];
-        return (I.f0[a] - o) + x * (float)B.inv_h;
+        return (I.f0[a] - o) + x * B.inv_h_f;
     }
 };
 

@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
         const int sx = s_ti.start[0], sy = s_ti.start[1], sz = s_ti.start[2];
         const int vol = ex * ey * ez;
         const int n = s_B.n;
-        const float sd = density ? (float)s_B.scale : 1.f;
+        const float sd = density ? s_B.scale_f : 1.f;
         const double h3 = 1.0 / s_B.scale;
         const int beg = w.cand_off[tile], end = w.cand_off[tile + 1];
         // bound on |sum| per lattice: wmax * sum_k |F_k,d| * sd
@@ -475,69 +475,52 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
             s_scale[threadIdx.x] = sc;
         }
         __syncthreads();
-        if constexpr (KER == 0) {
-            // node units: the three MAC lattices share weights per axis (the
-            // lattice whose component is along the axis uses s, the other two
-            // s - 1/2), so 6 one-dimensional stencils serve all 192 points
-            const float inv_h = (float)s_B.inv_h;
-            const float g0 = sd * s_scale[0], g1 = sd * s_scale[1], g2 = sd * s_scale[2];
+#pragma unroll 1
+        for (int d = 0; d < 3; ++d) {
+            Acc *accd = acc + d * vol;
+            const float gsc = sd * s_scale[d];
             for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
                 const int node = w.cand_nodes[q];
                 const InstDev &I = b.inst[b.node_inst[node]];
-                float ph[2][3][4];   // [shifted][axis][m]
-                int l[2][3][4];
+                const float gq = F[d * N + node] * gsc;
+                if constexpr (KER == 0) {
+                    float ph[3][4];
+                    int l[3][4];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const float t = I.f0[a] + x[a * N + node] * inv_h;
-                    const int st = a == 0 ? sx : (a == 1 ? sy : sz);
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int base = wrap_near(I.I0[a] + peskin_axis_fast(h ? t - 0.5f : t, ph[h][a]), n);
+                    for (int a = 0; a < 3; ++a) {
+                        const int I0 = I.I0[a];
+                        const float s = (I.f0[a] - (a == d ? 0.f : 0.5f)) + x[a * N + node] * s_B.inv_h_f;
+                        const int base = wrap_near(I0 + peskin_axis_fast(s, ph[a]), n);
+                        const int st = a == 0 ? sx : (a == 1 ? sy : sz);
 #pragma unroll
                         for (int m = 0; m < 4; ++m) {
                             int idx = base + m;
                             idx -= idx >= n ? n : 0;
-                            l[h][a][m] = idx - st;
+                            l[a][m] = idx - st;
                         }
                     }
-                }
-                const float gq[3] = {F[node] * g0, F[N + node] * g1, F[2 * N + node] * g2};
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const int hx = d == 0 ? 0 : 1, hy = d == 1 ? 0 : 1, hz = d == 2 ? 0 : 1;
-                    Acc *accd = acc + d * vol;
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        if ((unsigned)l[hz][2][c] >= (unsigned)ez)
+                        if ((unsigned)l[2][c] >= (unsigned)ez)
                             continue;
-                        const float wz = ph[hz][2][c] * gq[d];
+                        const float wz = ph[2][c] * gq;
 #pragma unroll
                         for (int bb = 0; bb < 4; ++bb) {
-                            if ((unsigned)l[hy][1][bb] >= (unsigned)ey)
+                            if ((unsigned)l[1][bb] >= (unsigned)ey)
                                 continue;
-                            const float wyz = ph[hy][1][bb] * wz;
-                            Acc *rp = accd + (l[hz][2][c] * ey + l[hy][1][bb]) * ex;
+                            const float wyz = ph[1][bb] * wz;
+                            Acc *rp = accd + (l[2][c] * ey + l[1][bb]) * ex;
 #pragma unroll
                             for (int a = 0; a < 4; ++a)
-                                if ((unsigned)l[hx][0][a] < (unsigned)ex)
-                                    acc_add(rp + l[hx][0][a], FixedPoint<Acc>::conv(ph[hx][0][a] * wyz));
+                                if ((unsigned)l[0][a] < (unsigned)ex)
+                                    acc_add(rp + l[0][a], FixedPoint<Acc>::conv(ph[0][a] * wyz));
                         }
                     }
-                }
-            }
-        } else {
-#pragma unroll 1
-        for (int d = 0; d < 3; ++d) {
-            Acc *accd = acc + d * vol;
-            const float gsc = sd * s_scale[d];            for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
-                const int node = w.cand_nodes[q];
-                const InstDev &I = b.inst[b.node_inst[node]];
-                const float gq = F[d * N + node] * gsc;
-                {
+                } else {
                     float s[3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
-                        s[a] = (I.f0[a] - (a == d ? 0.f : 0.5f)) + x[a * N + node] * (float)s_B.inv_h;
+                        s[a] = (I.f0[a] - (a == d ? 0.f : 0.5f)) + x[a * N + node] * s_B.inv_h_f;
                     int base[3];
                     float wt[27];
                     if (!mls_weights<float>(s, support, base, wt)) {
@@ -569,7 +552,6 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
                                             FixedPoint<Acc>::conv(wt[J] * gq));
                 }
             }
-        }
         }
         __syncthreads();
         // flush: per lattice, (z, y) planes of the tile over warps, x*y flat over lanes;
