@@ -330,6 +330,29 @@ __device__ __forceinline__ long long peskin_axis(real s, real ph[4])
     return i0;
 }
 
+// Per-thread partial sums as unevaluated float pairs (hi + lo, Knuth's
+// TwoSum and the FMA product error): about 44 significant bits, at FP32
+// speed; the FP64 pipe of this GPU is far narrower than its FP32 pipe.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ void df_add(DF &x, float v)
+{
+    const float s = x.hi + v;
+    const float bv = s - x.hi;
+    const float e = (x.hi - (s - bv)) + (v - bv);
+    const float t = x.lo + e;
+    x.hi = s + t;
+    x.lo = t - (x.hi - s);
+}
+__device__ __forceinline__ void df_add_prod(DF &x, float a, float b)
+{
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);
+    df_add(x, p);
+    x.lo += pe;
+}
+
 // ---------------------------------------------------- spread, FP32 fast
 // One CTA per active tile, tiles taken from a global counter. Contributions
 // are accumulated in shared memory as fixed-point integers (Acc = int or
@@ -562,7 +585,7 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
 #pragma unroll 1
         for (int d = 0; d < 3; ++d) {
             const float inv = 1.f / s_scale[d];
-            double part = 0.0;
+            DF part{0.f, 0.f};
             float *fd = f + s_B.grid_off + d * n3;
             for (int lz = wid; lz < ez; lz += nw) {
                 Acc *src = acc + d * vol + lz * plane;
@@ -575,16 +598,17 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
                         const float val = (float)q * inv;
                         float *p = dz + ly * n + (i - ly * ex);
                         *p += val;
-                        part += (double)val;
+                        df_add(part, val);
                         ++touched;
                     }
                 }
             }
+            double pd = (double)part.hi + (double)part.lo;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
-                part += __shfl_down_sync(0xffffffffu, part, o);
+                pd += __shfl_down_sync(0xffffffffu, pd, o);
             if (lane == 0)
-                s_red[d][wid] = part;
+                s_red[d][wid] = pd;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
@@ -1001,29 +1025,6 @@ __device__ inline double block_sum(double v, double *sh)
     double r = sh[0];
     __syncthreads();
     return r;
-}
-
-// Per-thread partial sums as unevaluated float pairs (hi + lo, Knuth's
-// TwoSum and the FMA product error): about 44 significant bits, at FP32
-// speed; the FP64 pipe of this GPU is far narrower than its FP32 pipe.
-struct DF {
-    float hi, lo;
-};
-__device__ __forceinline__ void df_add(DF &x, float v)
-{
-    const float s = x.hi + v;
-    const float bv = s - x.hi;
-    const float e = (x.hi - (s - bv)) + (v - bv);
-    const float t = x.lo + e;
-    x.hi = s + t;
-    x.lo = t - (x.hi - s);
-}
-__device__ __forceinline__ void df_add_prod(DF &x, float a, float b)
-{
-    const float p = a * b;
-    const float pe = fmaf(a, b, -p);
-    df_add(x, p);
-    x.lo += pe;
 }
 
 // One pass per instance: partial sums of x, F, v and x (x) F (about the
