@@ -270,6 +270,35 @@ int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, c
  * ifem_compute_forces: (dF/dx)^T g = -H g (H symmetric). */
 int ifem_force_hvp(ifem_ctx ctx, ifem_batch b, const void *x, const void *w, void *Hw, void *stream);
 
+/* ifem_compute_forces without any allocation in the call (the paper has no
+ * counterpart: this is a deployment variant of Algorithm step 1).
+ * Some callers must not allocate device memory while they run: code recorded
+ * into a CUDA graph under global stream capture, where cudaMalloc is not
+ * allowed; hosts that hand all device memory to their own pool or allocator
+ * up front; real-time loops that forbid allocation after start-up. This entry
+ * point computes the same forces as ifem_compute_forces through the
+ * deterministic element-buffer path (per-element forces, then a per-node sum
+ * in ascending element order, then the bending passes), taking its scratch
+ * from one fixed array of 32 MiB in device memory that the library declares
+ * at file scope: every GPU that loads libifem holds it until the process
+ * exits. It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   Limit: 12 reals per element plus 6 reals per node (reals of the
+ *   context's precision; the node part starts at a 256-byte boundary) must
+ *   fit in 32 MiB, e.g. about 600k triangles in IFEM_FP32; larger batches
+ *   are rejected with IFEM_ERR_CAPACITY before anything is launched.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Sharing: every call on a device uses the same array, which keeps the
+ *   last call's contents; each call writes every entry it later reads, so
+ *   nothing needs clearing. Calls whose kernels overlap on the GPU (other
+ *   streams, other threads) race on the array: serialise them.
+ * Arguments, layouts, stream semantics and status reporting are those of
+ * ifem_compute_forces; the FP32 results are deterministic but may differ in
+ * the last bits from ifem_compute_forces (this path uses no fused
+ * multiply-add). */
+int ifem_compute_forces_noalloc(ifem_ctx ctx, ifem_batch b, const void *x, void *F, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,11 +1,12 @@
 """Build libifem.so (the CUDA kernels behind include/ifem.h) for sm_103a.
 
-Three translation units are compiled in parallel with nvcc and linked into
+Four translation units are compiled in parallel with nvcc and linked into
 ``paper_1807_08219_gb300/_build/libifem.so``:
   api.cu          host code (handles, checks, FP64 reference data), host
                   compiler with -ffp-contract=off
   kernels_f32.cu  FP32 kernels (FMA contraction allowed)
   kernels_f64.cu  FP64 deterministic kernels, --fmad=false
+  noalloc.cu      the allocation-free force entry point, --fmad=false
 """
 from __future__ import annotations
 
@@ -25,6 +26,7 @@ UNITS = {
     "api.cu": [],
     "kernels_f32.cu": [],
     "kernels_f64.cu": ["--fmad=false"],
+    "noalloc.cu": ["--fmad=false"],
 }
 
 

@@ -35,7 +35,7 @@ EXPORTS = (
     "ifem_grid_create", "ifem_grid_destroy", "ifem_grid_values", "ifem_grid_box_offset",
     "ifem_batch_create", "ifem_batch_destroy", "ifem_batch_nodes", "ifem_batch_instances",
     "ifem_batch_set_origins", "ifem_prepare", "ifem_compute_forces", "ifem_spread", "ifem_interpolate",
-    "ifem_reduce", "ifem_step_coupling", "ifem_force_hvp",
+    "ifem_reduce", "ifem_step_coupling", "ifem_force_hvp", "ifem_compute_forces_noalloc",
 )
 
 
@@ -114,6 +114,7 @@ def load(build_if_missing: bool = True):
         "ifem_reduce": (i, [p, p, p, p, p, p, p]),
         "ifem_step_coupling": (i, [p, p, p, p, p, p, p, p, p, i, p]),
         "ifem_force_hvp": (i, [p, p, p, p, p, p]),
+        "ifem_compute_forces_noalloc": (i, [p, p, p, p, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -261,6 +262,11 @@ def ifem_prepare(ctx, b, x=None, stream=None):
 
 def ifem_compute_forces(ctx, b, x, F, stream=None):
     return _check(ctx, load().ifem_compute_forces(ctx, b, _ptr(x), _ptr(F), _stream(stream)))
+
+
+def ifem_compute_forces_noalloc(ctx, b, x, F, stream=None):
+    """ifem_compute_forces without allocation in the call (fixed 32 MiB device scratch)."""
+    return _check(ctx, load().ifem_compute_forces_noalloc(ctx, b, _ptr(x), _ptr(F), _stream(stream)))
 
 
 def ifem_spread(ctx, b, g, x, F, f, flags: int = 0, stream=None):
