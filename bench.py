@@ -167,7 +167,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ifem", choices=["ifem", "reference"])
     ap.add_argument("--scatter", default="atomic", choices=["atomic", "det"])
-    ap.add_argument("--tile", type=int, default=8)
+    ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

@@ -90,7 +90,7 @@ extern "C" int ifem_ctx_create(const ifem_config *cfg, ifem_ctx *out)
     ctx->cfg = *cfg;
     if (!(ctx->cfg.mls_support > 0.0))
         ctx->cfg.mls_support = std::sqrt(3.0);
-    ctx->tile = cfg->tile ? cfg->tile : 8;
+    ctx->tile = cfg->tile ? cfg->tile : 16;
     // FP32 spread accumulator width (tuning knob): IFEM_SPREAD_ACC=64 selects
     // 64-bit fixed point (slower shared-memory atomics), anything else 32-bit
     if (const char *acc = std::getenv("IFEM_SPREAD_ACC"))
@@ -601,7 +601,7 @@ static int ws_ensure(ifem_ctx ctx, ifem_batch b, ifem_grid g, int tile)
     }
     if (max_edge > kMaxTileEdge * 2)
         return fail(ctx, IFEM_ERR_CAPACITY, "tile edge too large");
-    if (nt >= (1LL << 31) - 1)
+    if (nt * kOwnSub3 >= (1LL << 31) - 1)
         return fail(ctx, IFEM_ERR_CAPACITY, "too many tiles");
     auto alloc = [&](void **p, size_t bytes) -> cudaError_t {
         cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
@@ -612,7 +612,8 @@ static int ws_ensure(ifem_ctx ctx, ifem_batch b, ifem_grid g, int tile)
     DevWork &w = ws.w;
     w = DevWork{};
     long long N = b->N;
-    int nb = (int)((nt + kScanBlock - 1) / kScanBlock);
+    const long long no = nt * kOwnSub3;
+    int nb = (int)((no + kScanBlock - 1) / kScanBlock);
     w.cand_cap = 8 * N;
     CK(alloc((void **)&ws.d_boxes, sizeof(BoxDev) * boxes.size()));
     CK(cudaMemcpy(ws.d_boxes, boxes.data(), sizeof(BoxDev) * boxes.size(), cudaMemcpyHostToDevice));
@@ -620,12 +621,11 @@ static int ws_ensure(ifem_ctx ctx, ifem_batch b, ifem_grid g, int tile)
     CK(alloc((void **)&w.cand_off, sizeof(int) * (nt + 1)));
     CK(alloc((void **)&w.cand_cursor, sizeof(int) * (nt + 1)));
     CK(alloc((void **)&w.cand_nodes, sizeof(int) * (size_t)w.cand_cap));
-    CK(alloc((void **)&w.own_count, sizeof(int) * (nt + 1)));
-    CK(alloc((void **)&w.own_off, sizeof(int) * (nt + 1)));
-    CK(alloc((void **)&w.own_cursor, sizeof(int) * (nt + 1)));
+    CK(alloc((void **)&w.own_count, sizeof(int) * (no + 1)));
+    CK(alloc((void **)&w.own_off, sizeof(int) * (no + 1)));
+    CK(alloc((void **)&w.own_cursor, sizeof(int) * (no + 1)));
     CK(alloc((void **)&w.own_nodes, sizeof(int) * (size_t)std::max<long long>(N, 1)));
     CK(alloc((void **)&w.active, sizeof(int) * (nt + 1)));
-    CK(alloc((void **)&w.own_active, sizeof(int) * (nt + 1)));
     CK(alloc((void **)&w.counters, sizeof(int) * 8));
     CK(alloc((void **)&w.scan_blocks, sizeof(int) * 2 * (nb + 1)));
     CK(alloc((void **)&w.red_tile, sizeof(double) * 3 * (nt + 1)));

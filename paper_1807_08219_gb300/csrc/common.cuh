@@ -16,6 +16,8 @@
 namespace ifem {
 
 constexpr int kMaxTileEdge = 20;   // tile edge t + 4 at most (t <= 16)
+constexpr int kOwnSub = 5;         // own-list sub-blocks (4 cells) per tile axis (tile edge <= 20)
+constexpr int kOwnSub3 = kOwnSub * kOwnSub * kOwnSub;
 constexpr int kScanThreads = 512;  // tile-count scan: threads per block
 constexpr int kScanPer = 4;        // and values per thread
 constexpr int kScanBlock = kScanThreads * kScanPer;
@@ -100,13 +102,12 @@ struct DevWork {
     int *cand_cursor;   // n_tiles
     int *cand_nodes;    // pair list: node id per (tile, node) candidate pair
     long long cand_cap;
-    int *own_count;
+    int *own_count;     // per (tile, 4^3 sub-block): n_tiles * kOwnSub3 + 1
     int *own_off;
     int *own_cursor;
-    int *own_nodes;     // N entries: nodes grouped by the tile of their cell
+    int *own_nodes;     // N entries: nodes grouped by the tile (and sub-block) of their cell
     int *active;        // tiles with candidate pairs
-    int *own_active;    // tiles with own nodes
-    int *counters;      // [0] n_active, [1] n_own_active, [2] work counter, [3] work counter 2
+    int *counters;      // [0] n_active, [2] work counter, [4] total pairs, [5] total own nodes
     int *scan_blocks;   // block partial sums for the tile scan
     void *elem_buf;     // per element nodal forces (12 reals per element)
     void *bend_buf;     // per node bending scratch (A, kH, n[3], lap) 6 reals

@@ -63,7 +63,8 @@ cudaError_t bin_impl(const TransferArgs &a, int det_sort)
     const long long nt = a.g.n_tiles;
     cudaStream_t s = a.stream;
     cudaMemsetAsync(w.cand_count, 0, sizeof(int) * (nt + 1), s);
-    cudaMemsetAsync(w.own_count, 0, sizeof(int) * (nt + 1), s);
+    const long long no = nt * kOwnSub3;
+    cudaMemsetAsync(w.own_count, 0, sizeof(int) * (no + 1), s);
     cudaMemsetAsync(w.counters, 0, sizeof(int) * 8, s);
     IFEM_LAUNCH_CHECK();
     if (b.n_inst == 0 || b.N == 0)
@@ -71,13 +72,13 @@ cudaError_t bin_impl(const TransferArgs &a, int det_sort)
     dim3 gn((b.max_nodes + 255) / 256, b.n_inst);
     bin_kernel<real, false><<<gn, 256, 0, s>>>(b, a.g, w, (const real *)a.x);
     IFEM_LAUNCH_CHECK();
-    int nb = (int)((nt + kScanBlock - 1) / kScanBlock);
-    scan_local_kernel<<<nb, kScanThreads, 0, s>>>(nt, w.cand_count, w.own_count, w.cand_off, w.own_off,
+    int nb = (int)((no + kScanBlock - 1) / kScanBlock);
+    scan_local_kernel<<<nb, kScanThreads, 0, s>>>(nt, no, w.cand_count, w.own_count, w.cand_off, w.own_off,
                                                   w.scan_blocks);
     IFEM_LAUNCH_CHECK();
     scan_blocks_kernel<<<1, 1024, 0, s>>>(nb, w.scan_blocks, w.counters + 4);
     IFEM_LAUNCH_CHECK();
-    scan_finish_kernel<<<(unsigned)((nt + 1 + 255) / 256), 256, 0, s>>>(nt, w);
+    scan_finish_kernel<<<(unsigned)((no + 1 + 255) / 256), 256, 0, s>>>(nt, no, w);
     IFEM_LAUNCH_CHECK();
     bin_kernel<real, true><<<gn, 256, 0, s>>>(b, a.g, w, (const real *)a.x);
     IFEM_LAUNCH_CHECK();
@@ -101,7 +102,7 @@ cudaError_t spread_impl(const TransferArgs &a)
         const int E = a.g.max_edge;
         cudaMemsetAsync(a.w.counters + 2, 0, sizeof(int), s);
         size_t acc = a.acc64 ? sizeof(long long) : sizeof(int);
-        size_t sm = acc * 3 * (size_t)E * E * E;
+        size_t sm = acc * 3 * (size_t)acc_stride(E, E, E);
         auto kern = a.kernel == 0 ? (a.acc64 ? spread_fast_kernel<0, long long> : spread_fast_kernel<0, int>)
                                   : (a.acc64 ? spread_fast_kernel<1, long long> : spread_fast_kernel<1, int>);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -130,9 +130,14 @@ __global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restr
         tl[a][1] = tile_of(hi, B.t, B.T);
         nt[a] = tl[a][0] == tl[a][1] ? 1 : 2;
     }
-    const long long own = B.tile_base
-                          + ((long long)tile_of(c[2], B.t, B.T) * B.T + tile_of(c[1], B.t, B.T)) * B.T
-                          + tile_of(c[0], B.t, B.T);
+    // own lists are keyed by (tile, 4^3 sub-block of the tile): nodes then come
+    // out of the fill grouped by position, which keeps the interpolation's
+    // gathers of neighbouring lanes on shared cache lines
+    const int ox = tile_of(c[0], B.t, B.T), oy = tile_of(c[1], B.t, B.T), oz = tile_of(c[2], B.t, B.T);
+    const int sbx = (c[0] - tile_start(ox, B.t)) >> 2, sby = (c[1] - tile_start(oy, B.t)) >> 2,
+              sbz = (c[2] - tile_start(oz, B.t)) >> 2;
+    const long long own = (B.tile_base + ((long long)oz * B.T + oy) * B.T + ox) * kOwnSub3
+                          + (sbz * kOwnSub + sby) * kOwnSub + sbx;
     agg_append<FILL>(w.own_count, w.own_cursor, w.own_nodes, own, ok, node);
 #pragma unroll
     for (int slot = 0; slot < 8; ++slot) {
@@ -180,8 +185,9 @@ __device__ inline int block_exclusive_scan(int v, int *sh, int &total)
     return r;
 }
 
-static __global__ void scan_local_kernel(long long n, const int *__restrict__ c1, const int *__restrict__ c2,
-                                  int *__restrict__ o1, int *__restrict__ o2, int *__restrict__ bsum)
+static __global__ void scan_local_kernel(long long n1, long long n2, const int *__restrict__ c1,
+                                         const int *__restrict__ c2, int *__restrict__ o1, int *__restrict__ o2,
+                                         int *__restrict__ bsum)
 {
     __shared__ int sh[33];
     long long base = (long long)blockIdx.x * kScanBlock + (long long)threadIdx.x * kScanPer;
@@ -189,8 +195,8 @@ static __global__ void scan_local_kernel(long long n, const int *__restrict__ c1
 #pragma unroll
     for (int q = 0; q < kScanPer; ++q) {
         long long i = base + q;
-        v1[q] = i < n ? c1[i] : 0;
-        v2[q] = i < n ? c2[i] : 0;
+        v1[q] = i < n1 ? c1[i] : 0;
+        v2[q] = i < n2 ? c2[i] : 0;
         s1 += v1[q];
         s2 += v2[q];
     }
@@ -200,10 +206,10 @@ static __global__ void scan_local_kernel(long long n, const int *__restrict__ c1
 #pragma unroll
     for (int q = 0; q < kScanPer; ++q) {
         long long i = base + q;
-        if (i < n) {
+        if (i < n1)
             o1[i] = e1;
+        if (i < n2)
             o2[i] = e2;
-        }
         e1 += v1[q];
         e2 += v2[q];
     }
@@ -236,44 +242,42 @@ static __global__ void scan_blocks_kernel(int nb, int *__restrict__ bsum, int *_
     }
 }
 
-static __global__ void scan_finish_kernel(long long n, DevWork w)
+// n1 tiles (candidate lists), n2 own sub-blocks. Adds the block offsets,
+// sets the fill cursors, writes the terminal offsets and the list of tiles
+// with candidates (order irrelevant: tiles are processed independently).
+static __global__ void scan_finish_kernel(long long n1, long long n2, DevWork w)
 {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = n1 > n2 ? n1 : n2;
     if (i > n)
         return;
-    int blk = (int)(i / kScanBlock);
-    if (i == n) {
-        // terminal offsets
-        w.cand_off[n] = w.counters[4];
-        w.own_off[n] = w.counters[5];
-        return;
+    const int blk = (int)(i / kScanBlock);
+    if (i == n1)
+        w.cand_off[n1] = w.counters[4];
+    if (i == n2)
+        w.own_off[n2] = w.counters[5];
+    if (i < n2) {
+        const int o2 = w.own_off[i] + w.scan_blocks[2 * blk + 1];
+        w.own_off[i] = o2;
+        w.own_cursor[i] = o2;
     }
-    int c1 = w.cand_count[i], c2 = w.own_count[i];
-    int o1 = w.cand_off[i] + w.scan_blocks[2 * blk];
-    int o2 = w.own_off[i] + w.scan_blocks[2 * blk + 1];
-    w.cand_off[i] = o1;
-    w.own_off[i] = o2;
-    w.cand_cursor[i] = o1;
-    w.own_cursor[i] = o2;
-    // active lists (order irrelevant: every tile is processed independently)
-    unsigned m1 = __ballot_sync(__activemask(), c1 > 0);
-    unsigned m2 = __ballot_sync(__activemask(), c2 > 0);
+    int c1 = 0;
+    if (i < n1) {
+        c1 = w.cand_count[i];
+        const int o1 = w.cand_off[i] + w.scan_blocks[2 * blk];
+        w.cand_off[i] = o1;
+        w.cand_cursor[i] = o1;
+    }
+    const unsigned act = __activemask();
+    const unsigned m1 = __ballot_sync(act, c1 > 0);
     const int lane = threadIdx.x & 31;
-    int leader = __ffs(__activemask()) - 1;
-    int b1 = 0, b2 = 0;
-    if (lane == leader) {
-        if (m1)
-            b1 = atomicAdd(&w.counters[0], __popc(m1));
-        if (m2)
-            b2 = atomicAdd(&w.counters[1], __popc(m2));
-    }
-    b1 = __shfl_sync(__activemask(), b1, leader);
-    b2 = __shfl_sync(__activemask(), b2, leader);
-    unsigned below = (1u << lane) - 1u;
+    const int leader = __ffs(act) - 1;
+    int b1 = 0;
+    if (lane == leader && m1)
+        b1 = atomicAdd(&w.counters[0], __popc(m1));
+    b1 = __shfl_sync(act, b1, leader);
     if (c1 > 0)
-        w.active[b1 + __popc(m1 & below)] = (int)i;
-    if (c2 > 0)
-        w.own_active[b2 + __popc(m2 & below)] = (int)i;
+        w.active[b1 + __popc(m1 & ((1u << lane) - 1u))] = (int)i;
 }
 
 // Deterministic mode: sort each tile's candidate list by node id (bitonic
@@ -395,6 +399,25 @@ __device__ __forceinline__ int peskin_axis_fast(float s, float ph[4])
 }
 
 __device__ __forceinline__ void acc_add(int *p, int v) { atomicAdd(p, v); }
+
+// Fire-and-forget adds performed at L2 (no value returned, so the SM does not
+// wait for the line): the tile flush adds its sums to the grid this way.
+__device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(__cvta_generic_to_global(p)), "f"(a),
+                 "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+__device__ __forceinline__ void red_add(float *p, float a)
+{
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(a) : "memory");
+}
+
+// Shared-memory pitches of a tile accumulator: odd row and plane pitches
+// spread the atomics of neighbouring nodes over the 32 banks.
+__host__ __device__ inline int acc_px(int ex) { return ex | 1; }
+__host__ __device__ inline int acc_pp(int ey, int px) { return (ey * px) | 1; }
+__host__ __device__ inline int acc_stride(int ex, int ey, int ez) { return ez * acc_pp(ey, acc_px(ex)); }
 // two's-complement addition through the unsigned 64-bit atomic
 __device__ __forceinline__ void acc_add(long long *p, long long v)
 {
@@ -437,7 +460,7 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
     // accumulators start at zero; the flush of every tile clears what it read
     {
         const int E = g.max_edge;
-        for (int i = threadIdx.x; i < 3 * E * E * E; i += blockDim.x)
+        for (int i = threadIdx.x; i < 3 * acc_stride(E, E, E); i += blockDim.x)
             acc[i] = 0;
     }
     for (;;) {
@@ -455,7 +478,8 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
             break;
         const int ex = s_ti.edge[0], ey = s_ti.edge[1], ez = s_ti.edge[2];
         const int sx = s_ti.start[0], sy = s_ti.start[1], sz = s_ti.start[2];
-        const int vol = ex * ey * ez;
+        const int px = acc_px(ex), pp = acc_pp(ey, px);
+        const int vol = ez * pp;   // per-lattice stride of the padded accumulator
         const int n = s_B.n;
         const float sd = density ? s_B.scale_f : 1.f;
         const double h3 = 1.0 / s_B.scale;
@@ -532,7 +556,7 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
                             if ((unsigned)l[1][bb] >= (unsigned)ey)
                                 continue;
                             const float wyz = ph[1][bb] * wz;
-                            Acc *rp = accd + (l[2][c] * ey + l[1][bb]) * ex;
+                            Acc *rp = accd + l[2][c] * pp + l[1][bb] * px;
 #pragma unroll
                             for (int a = 0; a < 4; ++a)
                                 if ((unsigned)l[0][a] < (unsigned)ex)
@@ -571,34 +595,55 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
                             for (int a = 0; a < 3; ++a, ++J)
                                 if ((unsigned)l[2][c] < (unsigned)ez && (unsigned)l[1][bb] < (unsigned)ey &&
                                     (unsigned)l[0][a] < (unsigned)ex)
-                                    acc_add(accd + (l[2][c] * ey + l[1][bb]) * ex + l[0][a],
+                                    acc_add(accd + l[2][c] * pp + l[1][bb] * px + l[0][a],
                                             FixedPoint<Acc>::conv(wt[J] * gq));
                 }
             }
         }
         __syncthreads();
-        // flush: per lattice, (z, y) planes of the tile over warps, x*y flat over lanes;
-        // clears every value it reads
+        // flush: per lattice, every row (z, y) of the tile, x in quads when the
+        // rows are 16-byte aligned; non-zero sums are added to the grid with
+        // L2 reductions (each value belongs to this tile only) and cleared
         const long long n3 = (long long)n * n * n;
-        const int plane = ex * ey;
         unsigned touched = 0;
+        const bool vec = ((sx | n | ex) & 3) == 0;
+        const int nq = vec ? (ex >> 2) : ex;
+        const int items = ey * ez * nq;
 #pragma unroll 1
         for (int d = 0; d < 3; ++d) {
             const float inv = 1.f / s_scale[d];
             DF part{0.f, 0.f};
             float *fd = f + s_B.grid_off + d * n3;
-            for (int lz = wid; lz < ez; lz += nw) {
-                Acc *src = acc + d * vol + lz * plane;
-                float *dz = fd + (long long)(sz + lz) * n * n + (long long)sy * n + sx;
-                for (int i = lane; i < plane; i += 32) {
-                    const Acc q = src[i];
+            Acc *ad = acc + d * vol;
+            for (int item = threadIdx.x; item < items; item += blockDim.x) {
+                const int r = item / nq, qx = item - r * nq;
+                const int lz = r / ey, ly = r - lz * ey;
+                Acc *src = ad + lz * pp + ly * px;
+                float *dst = fd + ((long long)(sz + lz) * n + (sy + ly)) * n + sx;
+                if (vec) {
+                    const int x0 = qx << 2;
+                    const Acc q0 = src[x0], q1 = src[x0 + 1], q2 = src[x0 + 2], q3 = src[x0 + 3];
+                    if ((q0 | q1 | q2 | q3) != 0) {
+                        src[x0] = 0;
+                        src[x0 + 1] = 0;
+                        src[x0 + 2] = 0;
+                        src[x0 + 3] = 0;
+                        const float v0 = (float)q0 * inv, v1 = (float)q1 * inv, v2 = (float)q2 * inv,
+                                    v3 = (float)q3 * inv;
+                        red_add_v4(dst + x0, v0, v1, v2, v3);
+                        df_add(part, v0);
+                        df_add(part, v1);
+                        df_add(part, v2);
+                        df_add(part, v3);
+                        touched += (q0 != 0) + (q1 != 0) + (q2 != 0) + (q3 != 0);
+                    }
+                } else {
+                    const Acc q = src[qx];
                     if (q != 0) {
-                        src[i] = 0;
-                        const int ly = i / ex;
-                        const float val = (float)q * inv;
-                        float *p = dz + ly * n + (i - ly * ex);
-                        *p += val;
-                        df_add(part, val);
+                        src[qx] = 0;
+                        const float v = (float)q * inv;
+                        red_add(dst + qx, v);
+                        df_add(part, v);
                         ++touched;
                     }
                 }
