@@ -90,7 +90,10 @@ extern "C" int ifem_ctx_create(const ifem_config *cfg, ifem_ctx *out)
     ctx->cfg = *cfg;
     if (!(ctx->cfg.mls_support > 0.0))
         ctx->cfg.mls_support = std::sqrt(3.0);
-    ctx->tile = cfg->tile ? cfg->tile : 16;
+    // default tile edge: 16 cells for the FP32 kernels (fewer (tile, node)
+    // pairs), 8 for the deterministic FP64 spread (its cost grows with the
+    // candidates per tile times the values per tile)
+    ctx->tile = cfg->tile ? cfg->tile : (cfg->precision == IFEM_FP64 ? 8 : 16);
     // FP32 spread accumulator width (tuning knob): IFEM_SPREAD_ACC=64 selects
     // 64-bit fixed point (slower shared-memory atomics), anything else 32-bit
     if (const char *acc = std::getenv("IFEM_SPREAD_ACC"))

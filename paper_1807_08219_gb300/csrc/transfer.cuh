@@ -806,117 +806,116 @@ __global__ void __launch_bounds__(kDetThreads) spread_det_kernel(DevBatch b, Dev
         const int ex = ti.edge[0], ey = ti.edge[1], ez = ti.edge[2];
         const int vol = ex * ey * ez;
         const long long n3 = (long long)B.n * B.n * B.n;
-        if (vol > kDetThreads * kDetCells) {
-            if (threadIdx.x == 0)
-                status_add(w.status, ST_CAPACITY, 1);
-            continue;
-        }
-        double accv[kDetCells][3], init[kDetCells][3];
-        int cx[kDetCells], cy[kDetCells], cz[kDetCells];
+        double part[3] = {0.0, 0.0, 0.0};
+        // owned values in chunks of kDetThreads * kDetCells; each chunk walks
+        // every candidate of the tile in ascending node order
+        for (int cbase = 0; cbase < vol; cbase += kDetThreads * kDetCells) {
+            double accv[kDetCells][3], init[kDetCells][3];
+            int cx[kDetCells], cy[kDetCells], cz[kDetCells];
 #pragma unroll
-        for (int q = 0; q < kDetCells; ++q) {
-            int i = threadIdx.x + q * kDetThreads;
-            int lx = i % ex, ly = (i / ex) % ey, lz = i / (ex * ey);
-            cx[q] = ti.start[0] + lx;
-            cy[q] = ti.start[1] + ly;
-            cz[q] = ti.start[2] + lz;
+            for (int q = 0; q < kDetCells; ++q) {
+                int i = cbase + threadIdx.x + q * kDetThreads;
+                int lx = i % ex, ly = (i / ex) % ey, lz = i / (ex * ey);
+                cx[q] = ti.start[0] + lx;
+                cy[q] = ti.start[1] + ly;
+                cz[q] = ti.start[2] + lz;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                double v = 0.0;
-                if (i < vol)
-                    v = f[B.grid_off + d * n3 + ((long long)cz[q] * B.n + cy[q]) * B.n + cx[q]];
-                accv[q][d] = v;
-                init[q][d] = v;
-            }
-        }
-        const double scale = density ? B.scale : 1.0;
-        const int beg = w.cand_off[tile], end = w.cand_off[tile + 1];
-        for (int c0 = beg; c0 < end; c0 += kDetChunk) {
-            const int nc = min(kDetChunk, end - c0);
-            __syncthreads();
-            // stage candidate data: one thread per (candidate, lattice)
-            for (int t = threadIdx.x; t < nc * 3; t += blockDim.x) {
-                const int j = t / 3, d = t % 3;
-                const int node = w.cand_nodes[c0 + j];
-                const InstDev I = b.inst[b.node_inst[node]];
-                DetCand<KER> &C = cand[j];
-                double s[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    int I0;
-                    s[a] = LatCoord<double>::get(I, B, a, x[a * N + node], (double)mac_off(d, a), I0);
+                for (int d = 0; d < 3; ++d) {
+                    double v = 0.0;
+                    if (i < vol)
+                        v = f[B.grid_off + d * n3 + ((long long)cz[q] * B.n + cy[q]) * B.n + cx[q]];
+                    accv[q][d] = v;
+                    init[q][d] = v;
                 }
-                if (d == 0) {
-                    C.ok = 1;
+            }
+            const double scale = density ? B.scale : 1.0;
+            const int beg = w.cand_off[tile], end = w.cand_off[tile + 1];
+            for (int c0 = beg; c0 < end; c0 += kDetChunk) {
+                const int nc = min(kDetChunk, end - c0);
+                __syncthreads();
+                // stage candidate data: one thread per (candidate, lattice)
+                for (int t = threadIdx.x; t < nc * 3; t += blockDim.x) {
+                    const int j = t / 3, d = t % 3;
+                    const int node = w.cand_nodes[c0 + j];
+                    const InstDev I = b.inst[b.node_inst[node]];
+                    DetCand<KER> &C = cand[j];
+                    double s[3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         int I0;
-                        double sc = LatCoord<double>::get(I, B, a, x[a * N + node], 0.0, I0);
-                        C.lo[a] = wrapi((long long)floor(sc) - 2, B.n);
+                        s[a] = LatCoord<double>::get(I, B, a, x[a * N + node], (double)mac_off(d, a), I0);
+                    }
+                    if (d == 0) {
+                        C.ok = 1;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            int I0;
+                            double sc = LatCoord<double>::get(I, B, a, x[a * N + node], 0.0, I0);
+                            C.lo[a] = wrapi((long long)floor(sc) - 2, B.n);
+                        }
+                    }
+                    C.g[d] = F[d * N + node] * scale;
+                    if constexpr (KER == 0) {
+#pragma unroll
+                        for (int a = 0; a < 3; ++a)
+                            C.base[d][a] = wrapi(peskin_axis<double>(s[a], C.ph[d][a]), B.n);
+                    } else {
+                        int base[3];
+                        if (!mls_weights<double>(s, support, base, C.wt[d])) {
+                            status_add(w.status, ST_DOMAIN, 1);
+                            C.g[d] = 0.0;
+#pragma unroll
+                            for (int J = 0; J < 27; ++J)
+                                C.wt[d][J] = 0.0;
+                        }
+#pragma unroll
+                        for (int a = 0; a < 3; ++a)
+                            C.base[d][a] = wrapi(base[a], B.n);
                     }
                 }
-                C.g[d] = F[d * N + node] * scale;
-                if constexpr (KER == 0) {
+                __syncthreads();
+                for (int j = 0; j < nc; ++j) {
+                    const DetCand<KER> &C = cand[j];
 #pragma unroll
-                    for (int a = 0; a < 3; ++a)
-                        C.base[d][a] = wrapi(peskin_axis<double>(s[a], C.ph[d][a]), B.n);
-                } else {
-                    int base[3];
-                    if (!mls_weights<double>(s, support, base, C.wt[d])) {
-                        status_add(w.status, ST_DOMAIN, 1);
-                        C.g[d] = 0.0;
+                    for (int q = 0; q < kDetCells; ++q) {
+                        if (cbase + threadIdx.x + q * kDetThreads >= vol)
+                            break;
+                        int rx = cx[q] - C.lo[0], ry = cy[q] - C.lo[1], rz = cz[q] - C.lo[2];
+                        rx += rx < 0 ? B.n : 0;
+                        ry += ry < 0 ? B.n : 0;
+                        rz += rz < 0 ? B.n : 0;
+                        if (rx > 4 || ry > 4 || rz > 4)
+                            continue;
 #pragma unroll
-                        for (int J = 0; J < 27; ++J)
-                            C.wt[d][J] = 0.0;
-                    }
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-                        C.base[d][a] = wrapi(base[a], B.n);
-                }
-            }
-            __syncthreads();
-            for (int j = 0; j < nc; ++j) {
-                const DetCand<KER> &C = cand[j];
-#pragma unroll
-                for (int q = 0; q < kDetCells; ++q) {
-                    if (threadIdx.x + q * kDetThreads >= vol)
-                        break;
-                    int rx = cx[q] - C.lo[0], ry = cy[q] - C.lo[1], rz = cz[q] - C.lo[2];
-                    rx += rx < 0 ? B.n : 0;
-                    ry += ry < 0 ? B.n : 0;
-                    rz += rz < 0 ? B.n : 0;
-                    if (rx > 4 || ry > 4 || rz > 4)
-                        continue;
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        int mx = cx[q] - C.base[d][0], my = cy[q] - C.base[d][1], mz = cz[q] - C.base[d][2];
-                        mx += mx < 0 ? B.n : 0;
-                        my += my < 0 ? B.n : 0;
-                        mz += mz < 0 ? B.n : 0;
-                        if constexpr (KER == 0) {
-                            if (mx <= 3 && my <= 3 && mz <= 3) {
-                                double wgt = (C.ph[d][0][mx] * C.ph[d][1][my]) * C.ph[d][2][mz];
-                                accv[q][d] = accv[q][d] + wgt * C.g[d];
+                        for (int d = 0; d < 3; ++d) {
+                            int mx = cx[q] - C.base[d][0], my = cy[q] - C.base[d][1], mz = cz[q] - C.base[d][2];
+                            mx += mx < 0 ? B.n : 0;
+                            my += my < 0 ? B.n : 0;
+                            mz += mz < 0 ? B.n : 0;
+                            if constexpr (KER == 0) {
+                                if (mx <= 3 && my <= 3 && mz <= 3) {
+                                    double wgt = (C.ph[d][0][mx] * C.ph[d][1][my]) * C.ph[d][2][mz];
+                                    accv[q][d] = accv[q][d] + wgt * C.g[d];
+                                }
+                            } else {
+                                if (mx <= 2 && my <= 2 && mz <= 2)
+                                    accv[q][d] = accv[q][d] + C.wt[d][(mz * 3 + my) * 3 + mx] * C.g[d];
                             }
-                        } else {
-                            if (mx <= 2 && my <= 2 && mz <= 2)
-                                accv[q][d] = accv[q][d] + C.wt[d][(mz * 3 + my) * 3 + mx] * C.g[d];
                         }
                     }
                 }
             }
-        }
-        __syncthreads();
-        double part[3] = {0.0, 0.0, 0.0};
+            __syncthreads();
 #pragma unroll
-        for (int q = 0; q < kDetCells; ++q) {
-            int i = threadIdx.x + q * kDetThreads;
-            if (i >= vol)
-                break;
+            for (int q = 0; q < kDetCells; ++q) {
+                int i = cbase + threadIdx.x + q * kDetThreads;
+                if (i >= vol)
+                    break;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                f[B.grid_off + d * n3 + ((long long)cz[q] * B.n + cy[q]) * B.n + cx[q]] = accv[q][d];
-                part[d] += accv[q][d] - init[q][d];
+                for (int d = 0; d < 3; ++d) {
+                    f[B.grid_off + d * n3 + ((long long)cz[q] * B.n + cy[q]) * B.n + cx[q]] = accv[q][d];
+                    part[d] += accv[q][d] - init[q][d];
+                }
             }
         }
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
