@@ -167,7 +167,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ifem", choices=["ifem", "reference"])
     ap.add_argument("--scatter", default="atomic", choices=["atomic", "det"])
-    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--tile", type=int, default=0, help="tile edge; 0 = autotune (ifem_prepare)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
@@ -201,6 +201,10 @@ def main():
 
     def step(s):
         I.ifem_step_coupling(cp.ctx, cp.batch, cp.grid, x, u, F, f, v, red, 0, s)
+
+    # work buffers (and, with --tile 0, the tile autotuner) before capture
+    I.ifem_prepare(cp.ctx, cp.batch, x, stream)
+    tile = I.ifem_ctx_tile(cp.ctx)
 
     # first step outside capture: allocates the work buffers, gives the counts
     with torch.cuda.stream(stream):
@@ -247,7 +251,7 @@ def main():
     value = world * N / (t_ms * 1e-3)
 
     # per-stage times of the same step (profiled context, same stream, same flush)
-    cpp = I.Coupler(wl, precision=I.IFEM_FP32, scatter=scatter, tile=args.tile, device=local, profile=1)
+    cpp = I.Coupler(wl, precision=I.IFEM_FP32, scatter=scatter, tile=tile, device=local, profile=1)
     stages = {k: [] for k in ("bin", "forces", "spread", "interp", "reduce")}
     fp = cpp.zeros_grid()
     for it in range(args.warmup + args.steps):
@@ -295,7 +299,7 @@ def main():
     # FP64 deterministic GPU path on the same workload (reported beside)
     fp64 = None
     if not args.no_fp64:
-        c64 = I.Coupler(wl, precision=I.IFEM_FP64, tile=args.tile, device=local)
+        c64 = I.Coupler(wl, precision=I.IFEM_FP64, tile=0, device=local)
         x64 = c64.nodes_to_device(xl32.astype(np.float64))
         u64 = c64.grid_to_device(wl.u)
         F64, v64, f64 = c64.empty_nodes(), c64.empty_nodes(), c64.zeros_grid()
@@ -333,7 +337,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nodes": N, "particles": len(wl.instances), "grid": 256,
-                   "kernel": "peskin4", "scatter": args.scatter, "tile": args.tile, "cuda_graph": True,
+                   "kernel": "peskin4", "scatter": args.scatter, "tile": tile,
+                   "tile_autotuned": args.tile == 0, "cuda_graph": True,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "hbm_gbs_step": step_gbs,
         "step_roofline_frac": step_gbs / hbm,

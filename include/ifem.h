@@ -111,7 +111,7 @@ typedef struct {
     int precision;      /* ifem_precision */
     int kernel;         /* ifem_kernel */
     int scatter;        /* ifem_scatter */
-    int tile;           /* node-bin tile edge in cells, 6..16; 0 = autotune on first use */
+    int tile;           /* node-bin tile edge in cells, 6..16; 0 = autotune in ifem_prepare */
     double mls_support; /* MLS weight radius h_w in cells; <= 0 means sqrt(3) */
     int device;         /* CUDA device ordinal the context is bound to */
     int profile;        /* 1: ifem_step_coupling records CUDA events around each stage */
@@ -213,7 +213,13 @@ int ifem_batch_instances(ifem_batch b);
 int ifem_batch_set_origins(ifem_batch b, const double *origins);
 /* Allocate every work buffer that the compute calls on (ctx, b) need, so
  * that later calls allocate nothing (for example inside CUDA-graph capture).
- * Also runs the tile autotuner if ctx's tile is 0 (timed on `stream`). */
+ * If ctx was created with tile = 0 and has not been tuned yet, first run the
+ * tile autotuner: binning + spreading + interpolation of b at positions x
+ * (device node array, required then) are timed with CUDA events on `stream`
+ * for tile edges {8, 12, 16} (FP32) or {6, 8, 10} (FP64), and the fastest is
+ * kept (ifem_ctx_tile). Autotuning allocates temporary buffers and
+ * synchronises: call it outside stream capture. Without ifem_prepare, a
+ * context with tile = 0 uses 16 (FP32) or 8 (FP64). */
 int ifem_prepare(ifem_ctx ctx, ifem_batch b, const void *x, void *stream);
 
 /* --------------------------------------------------------------- compute */

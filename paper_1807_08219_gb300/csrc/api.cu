@@ -852,12 +852,91 @@ extern "C" int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const
     return IFEM_OK;
 }
 
+// Tile autotuner: time binning + spreading + interpolation of the batch at
+// its current positions x for each candidate tile edge (CUDA events on
+// `stream`, best of two after one warm-up run) and keep the fastest. Forces
+// for the spread are the batch's own (computed once); the velocity field is
+// zero (the gathers cost the same for any values). Temporary buffers are
+// allocated and freed here, so this must run outside stream capture.
+static int autotune(ifem_ctx ctx, ifem_batch b, const void *x, void *stream)
+{
+    ifem_grid g = b->grid0;
+    const size_t rs = real_size(ctx);
+    const std::vector<int> cand = ctx->cfg.precision == IFEM_FP64 ? std::vector<int>{6, 8, 10}
+                                                                   : std::vector<int>{8, 12, 16};
+    void *F = nullptr, *v = nullptr, *u = nullptr, *f = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = IFEM_OK;
+    float best_ms = 1e30f;
+    int best = ctx->tile;
+    auto cleanup = [&]() {
+        cudaFree(F);
+        cudaFree(v);
+        cudaFree(u);
+        cudaFree(f);
+        if (e0)
+            cudaEventDestroy(e0);
+        if (e1)
+            cudaEventDestroy(e1);
+    };
+    if (cudaMalloc(&F, std::max<size_t>(16, 3 * b->N * rs)) != cudaSuccess ||
+        cudaMalloc(&v, std::max<size_t>(16, 3 * b->N * rs)) != cudaSuccess ||
+        cudaMalloc(&u, g->total * rs) != cudaSuccess || cudaMalloc(&f, g->total * rs) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cleanup();
+        return fail(ctx, IFEM_ERR_OOM, "autotune: temporary allocation failed");
+    }
+    cudaMemsetAsync(u, 0, g->total * rs, s);
+    cudaMemsetAsync(f, 0, g->total * rs, s);
+    if ((rc = do_forces(ctx, b, x, F, nullptr, 0, stream)) != IFEM_OK) {
+        cleanup();
+        return rc;
+    }
+    for (int t : cand) {
+        if ((rc = ws_ensure(ctx, b, g, t)) != IFEM_OK)
+            break;
+        const int saved = ctx->tile;
+        ctx->tile = t;
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 3 && rc == IFEM_OK; ++rep) {
+            cudaEventRecord(e0, s);
+            if ((rc = do_bin(ctx, b, g, x, stream)) == IFEM_OK && (rc = do_spread(ctx, b, g, x, F, f, 0, stream)) == IFEM_OK)
+                rc = do_interp(ctx, b, u, x, v, stream);
+            cudaEventRecord(e1, s);
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                rc = fail(ctx, IFEM_ERR_CUDA, "autotune: event timing failed");
+            if (rep > 0)
+                tmin = std::min(tmin, ms);
+        }
+        ctx->tile = saved;
+        if (rc != IFEM_OK)
+            break;
+        if (tmin < best_ms) {
+            best_ms = tmin;
+            best = t;
+        }
+    }
+    cleanup();
+    // the timing runs added to the status block; clear it
+    cudaMemset(ctx->d_status, 0, sizeof(unsigned long long) * kStatusWords);
+    if (rc != IFEM_OK)
+        return rc;
+    ctx->tile = best;
+    ctx->tuned = 1;
+    return ws_ensure(ctx, b, g, best);
+}
+
 extern "C" int ifem_prepare(ifem_ctx ctx, ifem_batch b, const void *x, void *stream)
 {
     int rc = check_call(ctx, b, nullptr);
     if (rc != IFEM_OK)
         return rc;
-    (void)x;
-    (void)stream;
+    if (ctx->cfg.tile == 0 && !ctx->tuned && b->N > 0) {
+        if (!x)
+            return fail(ctx, IFEM_ERR_ARG, "prepare: autotuning needs positions x");
+        return autotune(ctx, b, x, stream);
+    }
     return ws_ensure(ctx, b, b->grid0, ctx->tile);
 }

@@ -22,6 +22,7 @@ struct ifem_ctx_s {
     int ev_ok = 0;
     int ev_recorded = 0;
     int acc64 = 0;
+    int tuned = 0;
 };
 
 struct ifem_tmpl_s {

@@ -163,6 +163,10 @@ def ifem_ctx_create(precision: int = IFEM_FP32, kernel: int = IFEM_KERNEL_PESKIN
     return h
 
 
+def ifem_ctx_tile(ctx) -> int:
+    return int(load().ifem_ctx_tile(ctx))
+
+
 def ifem_stage_times(ctx):
     ms = (ctypes.c_double * 5)()
     _check(ctx, load().ifem_stage_times(ctx, ms))

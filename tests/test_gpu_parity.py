@@ -222,3 +222,24 @@ def test_inverted_tet_is_counted_and_still_evaluated():
     assert ninv >= 1
     assert g["rc"] == -5 and g["stats"]["inverted_elements"] == ninv
     assert np.array_equal(g["F"], F)
+
+
+def test_autotuned_tile_matches_fixed_tile():
+    import torch
+    from paper_1807_08219_gb300 import ifem as I
+    w = rounded_workload(wl("C2"), np.float32)
+    cp = I.Coupler(w, precision=FP32, tile=0)
+    try:
+        x = cp.nodes_to_device(w.x_local_all())
+        I.ifem_prepare(cp.ctx, cp.batch, x)
+        assert I.ifem_ctx_tile(cp.ctx) in (8, 12, 16)
+        u = cp.grid_to_device(w.u)
+        F, v, f = cp.empty_nodes(), cp.empty_nodes(), cp.zeros_grid()
+        I.ifem_step_coupling(cp.ctx, cp.batch, cp.grid, x, u, F, f, v, None)
+        I.ifem_sync_status(cp.ctx)
+        g = {"F": cp.nodes_to_host(F), "v": cp.nodes_to_host(v), "f": cp.grid_to_host(f)}
+    finally:
+        cp.close()
+    o = oracle_step(w)
+    assert rel_l2(g["F"], o["F"]) < TOL_F and rel_l2(g["v"], o["v"]) < TOL_V
+    assert rel_l2(g["f"][0], o["f"][0]) < TOL_GRID
