@@ -606,7 +606,10 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
         // L2 reductions (each value belongs to this tile only) and cleared
         const long long n3 = (long long)n * n * n;
         unsigned touched = 0;
-        const bool vec = ((sx | n | ex) & 3) == 0;
+        // quads need 16-byte aligned rows: box field base, n, tile start and
+        // edge all multiples of 4 floats
+        const bool vec = ((sx | n | ex) & 3) == 0 &&
+                         ((reinterpret_cast<uintptr_t>(f + s_B.grid_off)) & 15) == 0;
         const int nq = vec ? (ex >> 2) : ex;
         const int items = ey * ez * nq;
 #pragma unroll 1
