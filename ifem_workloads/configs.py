@@ -333,7 +333,11 @@ def config5(seed: int = 1005, n_boxes: int = 64, nmin: int = 32, nmax: int = 96,
             c = occ.place(rng, occ.offsets(frac, inside, ext), max_tries)
             if c is None:
                 continue
-            x = templates[ti].X @ M.T + _jitter(rng, templates[ti].X.shape, 1e-4 * n * h)
+            x = templates[ti].X @ M.T
+            if templates[ti].kind == "membrane":
+                # solids get the affine map only: their thinnest slivers are
+                # ~0.02 cells high and would invert under positional noise
+                x = x + _jitter(rng, x.shape, 1e-4 * n * h)
             instances.append(Instance(ti, b, (c + frac) * h, x))
         us.append(sample_on_mac(fourier_modes(rng), n, box.L, dtype=np.float32))
     return Workload("C5", templates, instances, boxes, us, seed,
