@@ -163,8 +163,8 @@ def cpu_baseline_sample(wl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ifem", choices=["ifem", "reference"])
     ap.add_argument("--scatter", default="atomic", choices=["atomic", "det"])
     ap.add_argument("--tile", type=int, default=0, help="tile edge; 0 = autotune (ifem_prepare)")
