@@ -35,6 +35,12 @@ WORKLOAD = ("dense blood suspension: 500 RBC (2562 nodes, Skalak C=100 + bending
             "(512 nodes / 2058 tets, NH), 256^3 periodic MAC grid, Ht 0.20, 4-point delta")
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the current kernels on this workload (profiles/*_c4_fp32.md);
+# set an entry to None when its kernel changes.
+NCU_TRAFFIC = {"spread": 268.76e6, "interp": 257.84e6, "forces": 16.68e6, "bin": None}
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -345,7 +351,7 @@ def main():
         "stage_ms": stage_ms,
         "touched_values": T, "pairs": P,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / hbm, "traffic": NCU_TRAFFIC.get(dom), "peak_kind": peak_kind,
                      "algorithmic_bytes": ab[dom]},
         "cpu_baseline": cpu,
         "e2e": {"value": world * N / (e2e_ms * 1e-3), "unit": "nodes/s", "h2d_bytes_per_step": 12 * N,
