@@ -282,6 +282,16 @@ static int tmpl_upload(ifem_ctx ctx, ifem_tmpl t, int nv, const int32_t *el, con
     CK(upload(&t->d_ref_f, reff.data(), reff.size()));
     CK(upload(&t->d_inc_off, off.data(), off.size()));
     CK(upload(&t->d_inc_idx, idx.data(), idx.size()));
+    if (nv == 3) {
+        // vertex one-ring: for each incidence (element e, corner c), the next two
+        // corners of e in its orientation order
+        std::vector<int2> ring(idx.size());
+        for (size_t q = 0; q < idx.size(); ++q) {
+            const int e = idx[q] >> 2, c = idx[q] & 3;
+            ring[q] = make_int2(el[3 * e + (c + 1) % 3], el[3 * e + (c + 2) % 3]);
+        }
+        CK(upload(&t->d_ring, ring.data(), ring.size()));
+    }
     return IFEM_OK;
 }
 
@@ -388,6 +398,7 @@ extern "C" int ifem_tmpl_destroy(ifem_tmpl t)
     cudaFree(t->d_ref_f);
     cudaFree(t->d_inc_off);
     cudaFree(t->d_inc_idx);
+    cudaFree(t->d_ring);
     delete t;
     return IFEM_OK;
 }
@@ -512,6 +523,7 @@ extern "C" int ifem_batch_create(ifem_ctx ctx, int n_tmpl, const ifem_tmpl *tmpl
         d.ref_f = s->d_ref_f;
         d.inc_off = s->d_inc_off;
         d.inc_idx = s->d_inc_idx;
+        d.ring = s->d_ring;
         d.mu = s->mu;
         d.C = s->C;
         d.kb = s->kb;

@@ -45,6 +45,8 @@ struct TmplDev {
     const float *ref_f;    // FP32 copy of ref_d
     const int *inc_off;    // n_nodes + 1: incidence CSR offsets
     const int *inc_idx;    // element*4 + local vertex, ascending element id
+    const int2 *ring;      // membranes: per incidence, the other two vertices (j, k) of the
+                           // triangle in its orientation order starting at the vertex
     double mu, C, kb, c0, lam;
 };
 

@@ -454,16 +454,15 @@ __device__ inline void bend_vertex_pass1(const TmplDev &T, int k, Load ld, real 
 {
     real K[3] = {0, 0, 0}, nrm[3] = {0, 0, 0}, A = 0, ang = 0;
     for (int q = T.inc_off[k]; q < T.inc_off[k + 1]; ++q) {
-        int code = T.inc_idx[q];
-        int e = code >> 2, c = code & 3;
-        int v[3] = {T.elems[3 * e], T.elems[3 * e + 1], T.elems[3 * e + 2]};
+        // incident triangle rotated to start at this vertex: (k, j, l)
+        const int2 jk = T.ring[q];
+        const int c = 0, c1 = 1, c2 = 2;
         real p[3][3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-            ld(v[r], p[r]);
+        ld(k, p[0]);
+        ld(jk.x, p[1]);
+        ld(jk.y, p[2]);
         TriGeom<real> t;
         tri_geom(p, t);
-        int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
         real cj = t.dot[c1] / t.twoA, ck = t.dot[c2] / t.twoA;
         real eij[3], eik[3];
 #pragma unroll
@@ -508,18 +507,15 @@ __device__ inline void bend_vertex_pass2(const TmplDev &T, int k, Load ld, LoadH
     const real kH0 = real(-0.5) * (real)T.c0;
     real lap = 0;
     for (int q = T.inc_off[k]; q < T.inc_off[k + 1]; ++q) {
-        int code = T.inc_idx[q];
-        int e = code >> 2, c = code & 3;
-        int v[3] = {T.elems[3 * e], T.elems[3 * e + 1], T.elems[3 * e + 2]};
+        const int2 jk = T.ring[q];
         real p[3][3];
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-            ld(v[r], p[r]);
+        ld(k, p[0]);
+        ld(jk.x, p[1]);
+        ld(jk.y, p[2]);
         TriGeom<real> t;
         tri_geom(p, t);
-        int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
-        lap += (t.dot[c2] / t.twoA) * ((kHof(v[c1]) - kH0) - (kH - kH0))
-             + (t.dot[c1] / t.twoA) * ((kHof(v[c2]) - kH0) - (kH - kH0));
+        lap += (t.dot[2] / t.twoA) * ((kHof(jk.x) - kH0) - (kH - kH0))
+             + (t.dot[1] / t.twoA) * ((kHof(jk.y) - kH0) - (kH - kH0));
     }
     real L = lap / (real(2) * A);
     real dh = kH - kH0;
@@ -671,17 +667,14 @@ static __global__ void __launch_bounds__(512, 2) forces_fused_f32_kernel(DevBatc
             float lap = 0.f, nrm[3] = {0.f, 0.f, 0.f};
             const float kHk = kHs[k];
             for (int q = T.inc_off[k]; q < T.inc_off[k + 1]; ++q) {
-                const int code = T.inc_idx[q];
-                const int e = code >> 2, c = code & 3;
-                const int v[3] = {T.elems[3 * e], T.elems[3 * e + 1], T.elems[3 * e + 2]};
+                const int2 jk = T.ring[q];
                 float p[3][3];
-#pragma unroll
-                for (int r = 0; r < 3; ++r)
-                    ld(v[r], p[r]);
+                ld(k, p[0]);
+                ld(jk.x, p[1]);
+                ld(jk.y, p[2]);
                 TriGeom<float> t;
                 tri_geom(p, t);
-                const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
-                lap += (t.dot[c2] / t.twoA) * (kHs[v[c1]] - kHk) + (t.dot[c1] / t.twoA) * (kHs[v[c2]] - kHk);
+                lap += (t.dot[2] / t.twoA) * (kHs[jk.x] - kHk) + (t.dot[1] / t.twoA) * (kHs[jk.y] - kHk);
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
                     nrm[a] += t.fn[a];

@@ -36,6 +36,7 @@ struct ifem_tmpl_s {
     float *d_ref_f = nullptr;
     int *d_inc_off = nullptr;
     int *d_inc_idx = nullptr;
+    int2 *d_ring = nullptr;
 };
 
 struct ifem_grid_s {

@@ -143,6 +143,8 @@ __global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restr
     for (int slot = 0; slot < 8; ++slot) {
         const int ix = slot & 1, iy = (slot >> 1) & 1, iz = slot >> 2;
         const bool valid = ok && ix < nt[0] && iy < nt[1] && iz < nt[2];
+        if (!__any_sync(0xffffffffu, valid))
+            continue;   // most nodes meet one or two tiles: skip empty slots warp-wide
         const long long tile = B.tile_base + ((long long)tl[2][iz] * B.T + tl[1][iy]) * B.T + tl[0][ix];
         agg_append<FILL>(w.cand_count, w.cand_cursor, w.cand_nodes, tile, valid, node);
     }
@@ -679,7 +681,7 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
 // locality for the L1/L2-cached gathers): v = sum_z phi_z sum_y phi_y
 // sum_x phi_x u, one square root per axis, 32-bit row offsets.
 template <int KER>
-__global__ void __launch_bounds__(256) interp_direct_kernel(DevBatch b, DevGrid g, DevWork w,
+__global__ void __launch_bounds__(256, 6) interp_direct_kernel(DevBatch b, DevGrid g, DevWork w,
                                                             const float *__restrict__ u,
                                                             const float *__restrict__ x, float *__restrict__ v,
                                                             float support)
