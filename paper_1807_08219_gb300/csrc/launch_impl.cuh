@@ -102,7 +102,7 @@ cudaError_t spread_impl(const TransferArgs &a)
         const int E = a.g.max_edge;
         cudaMemsetAsync(a.w.counters + 2, 0, sizeof(int), s);
         size_t acc = a.acc64 ? sizeof(long long) : sizeof(int);
-        size_t sm = acc * (size_t)acc_elems(E);
+        size_t sm = acc * 3 * (size_t)acc_stride(E, E, E);
         auto kern = a.kernel == 0 ? (a.acc64 ? spread_fast_kernel<0, long long> : spread_fast_kernel<0, int>)
                                   : (a.acc64 ? spread_fast_kernel<1, long long> : spread_fast_kernel<1, int>);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -415,7 +415,11 @@ __device__ __forceinline__ void red_add(float *p, float a)
     asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(a) : "memory");
 }
 
-
+// Shared-memory pitches of a tile accumulator: odd row and plane pitches
+// spread the atomics of neighbouring nodes over the 32 banks.
+__host__ __device__ inline int acc_px(int ex) { return ex | 1; }
+__host__ __device__ inline int acc_pp(int ey, int px) { return (ey * px) | 1; }
+__host__ __device__ inline int acc_stride(int ex, int ey, int ez) { return ez * acc_pp(ey, acc_px(ex)); }
 // two's-complement addition through the unsigned 64-bit atomic
 __device__ __forceinline__ void acc_add(long long *p, long long v)
 {
@@ -434,42 +438,6 @@ __device__ __forceinline__ int wrap_near(int v, int n)
     return v;
 }
 
-// Accumulator pitches (in Acc elements) of a tile: rows of px, planes of pp.
-// Tiles at most 16 wide get px = 16 and pp = 4 (mod 32), so that one warp's
-// 4 x 4 x 2 block of a stencil (x + 16 y + 4 z, y in a parity pair) hits 32
-// different banks; wider (ragged) tiles use odd pitches.
-__host__ __device__ inline void acc_pitches(int ex, int ey, int &px, int &pp)
-{
-    if (ex <= 16) {
-        px = 16;
-        pp = ey * 16;
-        while ((pp & 31) != 4)
-            ++pp;
-    } else {
-        px = ex | 1;
-        pp = (ey * px) | 1;
-    }
-}
-// Shared-memory elements for the three lattices of any tile with edges <= E.
-__host__ __device__ inline int acc_elems(int E)
-{
-    int px, pp, best = 0;
-    for (int ex = 1; ex <= E; ++ex) {
-        acc_pitches(ex, E, px, pp);
-        best = pp > best ? pp : best;
-    }
-    return 3 * E * best;
-}
-
-// Per-unit record of the two-phase Peskin spread: local base index per axis,
-// scaled force, and the 4 weights per axis.
-struct SpreadRec {
-    int l0[3];
-    float gq;
-    float ph[3][4];
-};
-constexpr int kSpreadChunk = 256;
-
 template <int KER, typename Acc>
 __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g, DevWork w,
                                                           const float *__restrict__ x,
@@ -478,7 +446,6 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
 {
     extern __shared__ __align__(16) unsigned char spread_smem[];
     Acc *acc = reinterpret_cast<Acc *>(spread_smem);
-    __shared__ SpreadRec rec[KER == 0 ? kSpreadChunk : 1];
     __shared__ float s_part[3][8];
     __shared__ float s_scale[3];
     __shared__ double s_red[3][8];
@@ -493,9 +460,11 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
         status_add(w.status, ST_ACTIVE, (unsigned long long)n_active);
     }
     // accumulators start at zero; the flush of every tile clears what it read
-    const int n_acc = acc_elems(g.max_edge);
-    for (int i = threadIdx.x; i < n_acc; i += blockDim.x)
-        acc[i] = 0;
+    {
+        const int E = g.max_edge;
+        for (int i = threadIdx.x; i < 3 * acc_stride(E, E, E); i += blockDim.x)
+            acc[i] = 0;
+    }
     for (;;) {
         if (threadIdx.x == 0) {
             int it = atomicAdd(&w.counters[2], 1);
@@ -511,11 +480,9 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
             break;
         const int ex = s_ti.edge[0], ey = s_ti.edge[1], ez = s_ti.edge[2];
         const int sx = s_ti.start[0], sy = s_ti.start[1], sz = s_ti.start[2];
-        int px, pp;
-        acc_pitches(ex, ey, px, pp);
-        const int vol = ez * pp;   // per-lattice stride of the accumulator
+        const int px = acc_px(ex), pp = acc_pp(ey, px);
+        const int vol = ez * pp;   // per-lattice stride of the padded accumulator
         const int n = s_B.n;
-        const bool full[3] = {ex == n, ey == n, ez == n};   // single tile along the axis
         const float sd = density ? s_B.scale_f : 1.f;
         const double h3 = 1.0 / s_B.scale;
         const int beg = w.cand_off[tile], end = w.cand_off[tile + 1];
@@ -557,69 +524,48 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
             s_scale[threadIdx.x] = sc;
         }
         __syncthreads();
-        if constexpr (KER == 0) {
-            // lane -> stencil slots (mx, my, mz) and (mx, my + 2, mz)
-            const int mx = lane & 3, mz = (lane >> 2) & 3, my = lane >> 4;
 #pragma unroll 1
-            for (int d = 0; d < 3; ++d) {
-                Acc *accd = acc + d * vol;
-                const float gsc = sd * s_scale[d];
-                for (int c0 = beg; c0 < end; c0 += kSpreadChunk) {
-                    const int nc = min(kSpreadChunk, end - c0);
-                    // phase 1: one thread per unit writes its record
-                    if (threadIdx.x < nc) {
-                        const int node = w.cand_nodes[c0 + threadIdx.x];
-                        const InstDev &I = b.inst[b.node_inst[node]];
-                        SpreadRec &R = rec[threadIdx.x];
-                        R.gq = F[d * N + node] * gsc;
+        for (int d = 0; d < 3; ++d) {
+            Acc *accd = acc + d * vol;
+            const float gsc = sd * s_scale[d];
+            for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
+                const int node = w.cand_nodes[q];
+                const InstDev &I = b.inst[b.node_inst[node]];
+                const float gq = F[d * N + node] * gsc;
+                if constexpr (KER == 0) {
+                    float ph[3][4];
+                    int l[3][4];
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            const float s = (I.f0[a] - (a == d ? 0.f : 0.5f)) + x[a * N + node] * s_B.inv_h_f;
-                            float ph[4];
-                            const int base = wrap_near(I.I0[a] + peskin_axis_fast(s, ph), n);
-                            int l = base - (a == 0 ? sx : (a == 1 ? sy : sz));
-                            l += l < 0 ? n : 0;
-                            if (!full[a] && l >= n - 3)
-                                l -= n;   // stencil starts before the tile
-                            R.l0[a] = l;
+                    for (int a = 0; a < 3; ++a) {
+                        const int I0 = I.I0[a];
+                        const float s = (I.f0[a] - (a == d ? 0.f : 0.5f)) + x[a * N + node] * s_B.inv_h_f;
+                        const int base = wrap_near(I0 + peskin_axis_fast(s, ph[a]), n);
+                        const int st = a == 0 ? sx : (a == 1 ? sy : sz);
 #pragma unroll
-                            for (int m = 0; m < 4; ++m)
-                                R.ph[a][m] = ph[m];
+                        for (int m = 0; m < 4; ++m) {
+                            int idx = base + m;
+                            idx -= idx >= n ? n : 0;
+                            l[a][m] = idx - st;
                         }
                     }
-                    __syncthreads();
-                    // phase 2: one warp per unit, 32 distinct banks per atomic
-                    for (int u = wid; u < nc; u += nw) {
-                        const SpreadRec &R = rec[u];
-                        int lx = R.l0[0] + mx, lz = R.l0[2] + mz;
-                        if (full[0] && lx >= n)
-                            lx -= n;
-                        if (full[2] && lz >= n)
-                            lz -= n;
-                        const bool okxz = (unsigned)lx < (unsigned)ex && (unsigned)lz < (unsigned)ez;
-                        const float wxz = R.ph[0][mx] * R.ph[2][mz] * R.gq;
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            int ly = R.l0[1] + my + 2 * h;
-                            if (full[1] && ly >= n)
-                                ly -= n;
-                            if (okxz && (unsigned)ly < (unsigned)ey)
-                                acc_add(accd + lz * pp + ly * px + lx,
-                                        FixedPoint<Acc>::conv(wxz * R.ph[1][my + 2 * h]));
+                    for (int c = 0; c < 4; ++c) {
+                        if ((unsigned)l[2][c] >= (unsigned)ez)
+                            continue;
+                        const float wz = ph[2][c] * gq;
+#pragma unroll
+                        for (int bb = 0; bb < 4; ++bb) {
+                            if ((unsigned)l[1][bb] >= (unsigned)ey)
+                                continue;
+                            const float wyz = ph[1][bb] * wz;
+                            Acc *rp = accd + l[2][c] * pp + l[1][bb] * px;
+#pragma unroll
+                            for (int a = 0; a < 4; ++a)
+                                if ((unsigned)l[0][a] < (unsigned)ex)
+                                    acc_add(rp + l[0][a], FixedPoint<Acc>::conv(ph[0][a] * wyz));
                         }
                     }
-                    __syncthreads();
-                }
-            }
-        } else {
-#pragma unroll 1
-            for (int d = 0; d < 3; ++d) {
-                Acc *accd = acc + d * vol;
-                const float gsc = sd * s_scale[d];
-                for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
-                    const int node = w.cand_nodes[q];
-                    const InstDev &I = b.inst[b.node_inst[node]];
-                    const float gq = F[d * N + node] * gsc;
+                } else {
                     float s[3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a)
@@ -655,8 +601,8 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
                                             FixedPoint<Acc>::conv(wt[J] * gq));
                 }
             }
-            __syncthreads();
         }
+        __syncthreads();
         // flush: per lattice, every row (z, y) of the tile, x in quads when the
         // rows are 16-byte aligned; non-zero sums are added to the grid with
         // L2 reductions (each value belongs to this tile only) and cleared
