@@ -715,28 +715,21 @@ __global__ void __launch_bounds__(256, 6) interp_direct_kernel(DevBatch b, DevGr
                 else iz[m] = idx;
             }
         }
-        // rows of 4 values: two aligned 16-byte loads per row when the row does
-        // not wrap and the lattice rows are 16-byte aligned (half the L1 requests
-        // of four scalar loads), scalar loads otherwise
-        const int x0 = ix[0];
-        const bool vec = x0 + 3 < n && (n & 3) == 0 && (reinterpret_cast<uintptr_t>(ud) & 15) == 0;
-        const int k = x0 & 3;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             float accz = 0.f;
 #pragma unroll
             for (int bb = 0; bb < 4; ++bb) {
                 const float *row = ud + (iz[c] * n + iy[bb]) * n;
-                float v0, v1, v2, v3;
-                if (vec) {
-                    const float4 *q = reinterpret_cast<const float4 *>(row + (x0 - k));
-                    const float4 lo = __ldg(q);
-                    const float4 hi = k ? __ldg(q + 1) : lo;
-                    v0 = k == 0 ? lo.x : (k == 1 ? lo.y : (k == 2 ? lo.z : lo.w));
-                    v1 = k == 0 ? lo.y : (k == 1 ? lo.z : (k == 2 ? lo.w : hi.x));
-                    v2 = k == 0 ? lo.z : (k == 1 ? lo.w : (k == 2 ? hi.x : hi.y));
-                    v3 = k == 0 ? lo.w : (k == 1 ? hi.x : (k == 2 ? hi.y : hi.z));
-                } else {
+                float accy = ph[0][0] * __ldg(row + ix[0]);
+#pragma unroll
+                for (int a = 1; a < 4; ++a)
+                    accy += ph[0][a] * __ldg(row + ix[a]);
+                accz += ph[1][bb] * accy;
+            }
+            out += ph[2][c] * accz;
+        }
+    } else {
                     v0 = __ldg(row + ix[0]);
                     v1 = __ldg(row + ix[1]);
                     v2 = __ldg(row + ix[2]);
