@@ -730,17 +730,6 @@ __global__ void __launch_bounds__(256, 6) interp_direct_kernel(DevBatch b, DevGr
             out += ph[2][c] * accz;
         }
     } else {
-                    v0 = __ldg(row + ix[0]);
-                    v1 = __ldg(row + ix[1]);
-                    v2 = __ldg(row + ix[2]);
-                    v3 = __ldg(row + ix[3]);
-                }
-                const float accy = ph[0][0] * v0 + ph[0][1] * v1 + ph[0][2] * v2 + ph[0][3] * v3;
-                accz += ph[1][bb] * accy;
-            }
-            out += ph[2][c] * accz;
-        }
-    } else {
         float s[3];
         int I0[3];
 #pragma unroll
