@@ -113,6 +113,21 @@ def algorithmic_bytes(N, T, P, real=4):
     }
 
 
+def max_over_ranks(values, device, dist=None):
+    """Element-wise maximum of per-rank timings (ms) over all ranks."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_throughput(n_nodes_per_rank, world, t_ms):
+    """Whole-job nodes per second: every rank couples its own replica in t_ms."""
+    return world * n_nodes_per_rank / (t_ms * 1e-3)
+
+
 def run_reference(args, rank, world):
     """The FP64 CPU oracle on the same workload (rank 0 only)."""
     if rank != 0:
@@ -249,12 +264,8 @@ def main():
         dist.barrier()
     wall = time.perf_counter() - t_wall0
     ck = clocks.stop()
-    t_ms = float(np.mean(times))
-    if dist:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = world * N / (t_ms * 1e-3)
+    t_ms = max_over_ranks([float(np.mean(times))], dev, dist)[0]
+    value = job_throughput(N, world, t_ms)
 
     # per-stage times of the same step (profiled context, same stream, same flush)
     cpp = I.Coupler(wl, precision=I.IFEM_FP32, scatter=scatter, tile=tile, device=local, profile=1)
@@ -296,11 +307,7 @@ def main():
         e1.synchronize()
         if it >= args.warmup:
             e2e.append(e0.elapsed_time(e1))
-    e2e_ms = float(np.mean(e2e))
-    if dist:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks([float(np.mean(e2e))], dev, dist)[0]
 
     # FP64 deterministic GPU path on the same workload (reported beside)
     fp64 = None
@@ -354,7 +361,7 @@ def main():
                      "frac": achieved / hbm, "traffic": NCU_TRAFFIC.get(dom), "peak_kind": peak_kind,
                      "algorithmic_bytes": ab[dom]},
         "cpu_baseline": cpu,
-        "e2e": {"value": world * N / (e2e_ms * 1e-3), "unit": "nodes/s", "h2d_bytes_per_step": 12 * N,
+        "e2e": {"value": job_throughput(N, world, e2e_ms), "unit": "nodes/s", "h2d_bytes_per_step": 12 * N,
                 "d2h_bytes_per_step": 12 * N + 8 * red.numel()},
         "fp64": fp64,
         "gpu_launches": launches_per_step * args.steps,
