@@ -38,7 +38,7 @@ WORKLOAD = ("dense blood suspension: 500 RBC (2562 nodes, Skalak C=100 + bending
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the current kernels on this workload (profiles/*_c4_fp32.md);
 # set an entry to None when its kernel changes.
-NCU_TRAFFIC = {"spread": 268.76e6, "interp": 257.84e6, "forces": 16.68e6, "bin": None}
+NCU_TRAFFIC = {"spread": 268.76e6, "interp": None, "forces": None, "bin": None}
 
 
 def peaks():
