@@ -100,9 +100,12 @@ class Clocks:
 
 
 def algorithmic_bytes(N, T, P, real=4):
-    """Algorithmic bytes per stage (measurement section).
+    """Algorithmic bytes per stage: the bytes each stage must move at least.
 
-    N nodes, T touched lattice values (3 lattices), P (tile, node) pairs."""
+    N nodes, T touched lattice values (over the 3 lattices), P (tile, node)
+    pairs, `real` bytes per value. Node arrays are read or written once per
+    stage; each touched lattice value is read once (interpolation) or read and
+    written once (spreading)."""
     return {
         "bin": 2 * 3 * real * N + 4 * (N + P),          # x read (count + fill), pair/own lists written
         "forces": 2 * 3 * real * N,                     # x read, F written
