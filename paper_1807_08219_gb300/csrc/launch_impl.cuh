@@ -132,8 +132,8 @@ cudaError_t interp_impl(const TransferArgs &a)
     if constexpr (std::is_same<real, float>::value) {
         unsigned grid = (unsigned)((3 * b.N + 255) / 256);
         if (a.kernel == 0)
-            interp_quad_kernel<<<(unsigned)((12 * b.N + 255) / 256), 256, 0, a.stream>>>(
-                b, a.g, a.w, (const float *)a.u, (const float *)a.x, (float *)a.v);
+            interp_direct_kernel<0><<<grid, 256, 0, a.stream>>>(b, a.g, a.w, (const float *)a.u, (const float *)a.x,
+                                                               (float *)a.v, (float)a.support);
         else
             interp_direct_kernel<1><<<grid, 256, 0, a.stream>>>(b, a.g, a.w, (const float *)a.u, (const float *)a.x,
                                                                (float *)a.v, (float)a.support);

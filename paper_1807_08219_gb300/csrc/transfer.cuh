@@ -676,63 +676,6 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
     }
 }
 
-// ------------------------------------------------- interp, FP32 quads
-// Four lanes per (node, lattice) unit: lane q of the quad gathers column
-// x0 + q of the 16 stencil rows, so one warp load covers 8 nodes x 4
-// contiguous values (half the L1 sectors of 32 nodes x 1 value), then the
-// quad sums its partials with two shuffles: v = sum_q phi_x[q] *
-// sum_z phi_z sum_y phi_y u.
-static __global__ void __launch_bounds__(256) interp_quad_kernel(DevBatch b, DevGrid g, DevWork w,
-                                                          const float *__restrict__ u,
-                                                          const float *__restrict__ x, float *__restrict__ v)
-{
-    const int total = w.counters[5];
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long unit = tid >> 2;
-    const int q = (int)(tid & 3);
-    const bool live = unit < 3LL * total;
-    float part = 0.f;
-    int d = 0, node = 0;
-    if (live) {
-        d = (int)(unit / total);
-        node = w.own_nodes[unit - (long long)d * total];
-        const InstDev I = b.inst[b.node_inst[node]];
-        const BoxDev B = g.boxes[I.box];
-        const long long N = b.N;
-        const int n = B.n;
-        const float *ud = u + B.grid_off + (long long)d * n * n * n;
-        float ph[3][4];
-        int base[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            int I0;
-            const float s = LatCoord<float>::get(I, B, a, x[a * N + node], mac_off(d, a), I0);
-            base[a] = wrap_near(I0 + peskin_axis_fast(s, ph[a]), n);
-        }
-        int xq = base[0] + q;
-        xq -= xq >= n ? n : 0;
-        float acc = 0.f;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            int z = base[2] + c;
-            z -= z >= n ? n : 0;
-            float accy = 0.f;
-#pragma unroll
-            for (int bb = 0; bb < 4; ++bb) {
-                int y = base[1] + bb;
-                y -= y >= n ? n : 0;
-                accy += ph[1][bb] * __ldg(ud + (z * n + y) * n + xq);
-            }
-            acc += ph[2][c] * accy;
-        }
-        part = (q == 0 ? ph[0][0] : q == 1 ? ph[0][1] : q == 2 ? ph[0][2] : ph[0][3]) * acc;
-    }
-    part += __shfl_xor_sync(0xffffffffu, part, 1);
-    part += __shfl_xor_sync(0xffffffffu, part, 2);
-    if (live && q == 0)
-        v[d * b.N + node] = part;
-}
-
 // ------------------------------------------------- interp, FP32 direct
 // Thread per (node, lattice) unit over the nodes in tile order (spatial
 // locality for the L1/L2-cached gathers): v = sum_z phi_z sum_y phi_y
