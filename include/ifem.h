@@ -265,7 +265,12 @@ int ifem_reduce(ifem_ctx ctx, ifem_batch b, const void *x, const void *F, const 
 
 /* The whole coupling step in one call: bin, forces -> F, spread F -> f
  * (flags as ifem_spread), interpolate u -> v, reductions -> red (may be
- * NULL). Equivalent to the four calls above in that order. */
+ * NULL). Gives the results of the four calls above. The forces run beside
+ * the binning and the interpolation beside the spreading, on two streams the
+ * context owns, forked from `stream` with events and joined back into it
+ * before the reductions (valid under CUDA-graph capture of `stream`); with
+ * cfg.profile = 1 the stages run one after the other on `stream` instead, so
+ * that ifem_stage_times can attribute them. */
 int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *u,
                        void *F, void *f, void *v, double *red, int flags, void *stream);
 

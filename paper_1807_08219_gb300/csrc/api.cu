@@ -108,6 +108,16 @@ extern "C" int ifem_ctx_create(const ifem_config *cfg, ifem_ctx *out)
         delete ctx;
         return IFEM_ERR_CUDA;
     }
+    for (int i = 0; i < 2; ++i)
+        if (cudaStreamCreateWithFlags(&ctx->aux[i], cudaStreamNonBlocking) != cudaSuccess) {
+            ifem_ctx_destroy(ctx);
+            return IFEM_ERR_CUDA;
+        }
+    for (int i = 0; i < 4; ++i)
+        if (cudaEventCreateWithFlags(&ctx->fork[i], cudaEventDisableTiming) != cudaSuccess) {
+            ifem_ctx_destroy(ctx);
+            return IFEM_ERR_CUDA;
+        }
     if (cfg->profile) {
         ctx->ev_ok = 1;
         for (int i = 0; i < 6; ++i)
@@ -125,6 +135,12 @@ extern "C" int ifem_ctx_destroy(ifem_ctx ctx)
     for (int i = 0; i < 6; ++i)
         if (ctx->ev[i])
             cudaEventDestroy(ctx->ev[i]);
+    for (int i = 0; i < 4; ++i)
+        if (ctx->fork[i])
+            cudaEventDestroy(ctx->fork[i]);
+    for (int i = 0; i < 2; ++i)
+        if (ctx->aux[i])
+            cudaStreamDestroy(ctx->aux[i]);
     cudaFree(ctx->d_status);
     cudaFreeHost(ctx->h_status);
     delete ctx;
@@ -844,23 +860,63 @@ extern "C" int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const
         return fail(ctx, IFEM_ERR_ARG, "step_coupling: null array or grid");
     if (flags & ~(IFEM_SPREAD_FORCE | IFEM_SPREAD_OVERWRITE))
         return fail(ctx, IFEM_ERR_ARG, "step_coupling: unknown flags");
-    mark(ctx, 0, stream);
+    if (ctx->ev_ok) {
+        // profiling: stages one after the other on the caller's stream, each
+        // bracketed by an event
+        mark(ctx, 0, stream);
+        if ((rc = do_bin(ctx, b, g, x, stream)) != IFEM_OK)
+            return rc;
+        mark(ctx, 1, stream);
+        if ((rc = do_forces(ctx, b, x, F, nullptr, 0, stream)) != IFEM_OK)
+            return rc;
+        mark(ctx, 2, stream);
+        if ((rc = do_spread(ctx, b, g, x, F, f, flags, stream)) != IFEM_OK)
+            return rc;
+        mark(ctx, 3, stream);
+        if ((rc = do_interp(ctx, b, u, x, v, stream)) != IFEM_OK)
+            return rc;
+        mark(ctx, 4, stream);
+        if (red && (rc = do_reduce(ctx, b, x, F, v, red, stream)) != IFEM_OK)
+            return rc;
+        mark(ctx, 5, stream);
+        ctx->ev_recorded = 1;
+        return IFEM_OK;
+    }
+    // fork-join over the context's two auxiliary streams (also inside stream
+    // capture): forces run beside binning, interpolation beside spreading
+    //   s:    bin ----------- wait(forces) spread  wait(interp) reduce
+    //   aux0: forces -------/
+    //   aux1:       wait(bin) interp -------------/
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = ws_ensure(ctx, b, g, ctx->tile)) != IFEM_OK)
+        return rc;
+    cudaError_t e = cudaEventRecord(ctx->fork[0], s);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(ctx->aux[0], ctx->fork[0], 0);
+    if (e != cudaSuccess)
+        return launch_rc(ctx, e, "step_coupling fork");
+    if ((rc = do_forces(ctx, b, x, F, nullptr, 0, ctx->aux[0])) != IFEM_OK)
+        return rc;
+    if ((e = cudaEventRecord(ctx->fork[1], ctx->aux[0])) != cudaSuccess)
+        return launch_rc(ctx, e, "step_coupling fork");
     if ((rc = do_bin(ctx, b, g, x, stream)) != IFEM_OK)
         return rc;
-    mark(ctx, 1, stream);
-    if ((rc = do_forces(ctx, b, x, F, nullptr, 0, stream)) != IFEM_OK)
+    if ((e = cudaEventRecord(ctx->fork[2], s)) == cudaSuccess)
+        e = cudaStreamWaitEvent(ctx->aux[1], ctx->fork[2], 0);
+    if (e != cudaSuccess)
+        return launch_rc(ctx, e, "step_coupling fork");
+    if ((rc = do_interp(ctx, b, u, x, v, ctx->aux[1])) != IFEM_OK)
         return rc;
-    mark(ctx, 2, stream);
+    if ((e = cudaEventRecord(ctx->fork[3], ctx->aux[1])) == cudaSuccess)
+        e = cudaStreamWaitEvent(s, ctx->fork[1], 0);
+    if (e != cudaSuccess)
+        return launch_rc(ctx, e, "step_coupling join");
     if ((rc = do_spread(ctx, b, g, x, F, f, flags, stream)) != IFEM_OK)
         return rc;
-    mark(ctx, 3, stream);
-    if ((rc = do_interp(ctx, b, u, x, v, stream)) != IFEM_OK)
-        return rc;
-    mark(ctx, 4, stream);
+    if ((e = cudaStreamWaitEvent(s, ctx->fork[3], 0)) != cudaSuccess)
+        return launch_rc(ctx, e, "step_coupling join");
     if (red && (rc = do_reduce(ctx, b, x, F, v, red, stream)) != IFEM_OK)
         return rc;
-    mark(ctx, 5, stream);
-    ctx->ev_recorded = ctx->ev_ok;
     return IFEM_OK;
 }
 

@@ -23,6 +23,8 @@ struct ifem_ctx_s {
     int ev_recorded = 0;
     int acc64 = 0;
     int tuned = 0;
+    cudaStream_t aux[2] = {};   // fork-join streams of ifem_step_coupling
+    cudaEvent_t fork[4] = {};
 };
 
 struct ifem_tmpl_s {
