@@ -31,8 +31,13 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "Lagrangian nodes coupled/s (force+spread+interp) and HBM GB/s; FP32-batched vs FP64 at stated err"
-WORKLOAD = ("dense blood suspension: 500 RBC (2562 nodes, Skalak C=100 + bending) + 100 platelets "
-            "(512 nodes / 2058 tets, NH), 256^3 periodic MAC grid, Ht 0.20, 4-point delta")
+WORKLOADS = {
+    "C4": ("dense blood suspension: 500 RBC (2562 nodes, Skalak C=100 + bending) + 100 platelets "
+           "(512 nodes / 2058 tets, NH), 256^3 periodic MAC grid, Ht 0.20, 4-point delta"),
+    "C5": ("batch of 64 independent periodic boxes (32^3..96^3 cells, h = 1/64) with 1-20 mixed particles "
+           "each (capsules 642/2562, RBC 2562, Kuhn balls 512-3375 nodes), one launch per stage, 4-point delta"),
+}
+WORKLOAD = WORKLOADS["C4"]
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
@@ -194,6 +199,8 @@ def main():
     ap.add_argument("--tile", type=int, default=0, help="tile edge; 0 = autotune (ifem_prepare)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="C4", choices=sorted(WORKLOADS),
+                    help="C4 (default, the headline suspension) or C5 (64 mixed boxes)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -209,7 +216,7 @@ def main():
     import ifem_workloads as W
     from paper_1807_08219_gb300 import ifem as I
 
-    wl = W.make("C4")
+    wl = W.make(args.workload)
     N = wl.n_nodes
     scatter = I.IFEM_SCATTER_ATOMIC if args.scatter == "atomic" else I.IFEM_SCATTER_DET
     cp = I.Coupler(wl, precision=I.IFEM_FP32, scatter=scatter, tile=args.tile, device=local)
@@ -219,7 +226,7 @@ def main():
     u = cp.grid_to_device(wl.u)
     F, v = cp.empty_nodes(), cp.empty_nodes()
     f = cp.zeros_grid()
-    red = torch.zeros(12 * len(wl.instances) + 6, dtype=torch.float64, device=dev)
+    red = torch.zeros(12 * len(wl.instances) + 6 * len(wl.boxes), dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.Stream(device=dev)
 
@@ -352,7 +359,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "nodes/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nodes": N, "particles": len(wl.instances), "grid": 256,
+        "config": {"workload": WORKLOADS[args.workload], "nodes": N, "particles": len(wl.instances),
+                   "grid": [b.n for b in wl.boxes] if len(wl.boxes) > 1 else wl.boxes[0].n,
                    "kernel": "peskin4", "scatter": args.scatter, "tile": tile,
                    "tile_autotuned": args.tile == 0, "cuda_graph": True,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
