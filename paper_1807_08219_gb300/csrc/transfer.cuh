@@ -386,13 +386,15 @@ struct FixedPoint<long long> {
 // r = s - floor(s) in [0, 1) and q = sqrt(1 + 4r - 4r^2),
 //   phi(1 + r) = (3 - 2r - q)/8, phi(r) = (3 - 2r + q)/8,
 //   phi(1 - r) = (1 + 2r + q)/8, phi(2 - r) = (1 + 2r - q)/8
-// (the radicands of both branches of phi reduce to the same 1 + 4r - 4r^2).
+// (the radicands of both branches of phi reduce to the same 1 + 4r - 4r^2,
+// which lies in [1, 2], so sqrt(t) = t * rsqrt(t) needs no special cases).
 // Used by the FP32 kernels; the FP64 kernels evaluate phi point by point.
 __device__ __forceinline__ int peskin_axis_fast(float s, float ph[4])
 {
     const float fl = floorf(s);
     const float r = s - fl;
-    const float q = sqrtf(fmaxf(1.f + 4.f * r - 4.f * r * r, 0.f));
+    const float t = 1.f + 4.f * r - 4.f * r * r;   // in [1, 2] for r in [0, 1)
+    const float q = t * rsqrtf(t);
     ph[0] = (3.f - 2.f * r - q) * 0.125f;
     ph[1] = (3.f - 2.f * r + q) * 0.125f;
     ph[2] = (1.f + 2.f * r + q) * 0.125f;
@@ -548,21 +550,29 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
                             l[a][m] = idx - st;
                         }
                     }
+                    // validity bit masks; every slot runs, the atomic is predicated
+                    // (no divergent branches around the 64 slots)
+                    unsigned okx = 0, oky = 0, okz = 0;
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        okx |= (unsigned)((unsigned)l[0][m] < (unsigned)ex) << m;
+                        oky |= (unsigned)((unsigned)l[1][m] < (unsigned)ey) << m;
+                        okz |= (unsigned)((unsigned)l[2][m] < (unsigned)ez) << m;
+                    }
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        if ((unsigned)l[2][c] >= (unsigned)ez)
-                            continue;
                         const float wz = ph[2][c] * gq;
 #pragma unroll
                         for (int bb = 0; bb < 4; ++bb) {
-                            if ((unsigned)l[1][bb] >= (unsigned)ey)
-                                continue;
                             const float wyz = ph[1][bb] * wz;
-                            Acc *rp = accd + l[2][c] * pp + l[1][bb] * px;
+                            const unsigned rowok = (okz >> c) & (oky >> bb) & 1u;
+                            const int row = l[2][c] * pp + l[1][bb] * px;
 #pragma unroll
-                            for (int a = 0; a < 4; ++a)
-                                if ((unsigned)l[0][a] < (unsigned)ex)
-                                    acc_add(rp + l[0][a], FixedPoint<Acc>::conv(ph[0][a] * wyz));
+                            for (int a = 0; a < 4; ++a) {
+                                const Acc qv = FixedPoint<Acc>::conv(ph[0][a] * wyz);
+                                if (rowok & (okx >> a))
+                                    acc_add(accd + row + l[0][a], qv);
+                            }
                         }
                     }
                 } else {
@@ -653,12 +663,15 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
                     }
                 }
             }
-            double pd = (double)part.hi + (double)part.lo;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-                pd += __shfl_down_sync(0xffffffffu, pd, o);
+            for (int o = 16; o > 0; o >>= 1) {
+                const float hi = __shfl_down_sync(0xffffffffu, part.hi, o);
+                const float lo = __shfl_down_sync(0xffffffffu, part.lo, o);
+                df_add(part, hi);
+                part.lo += lo;
+            }
             if (lane == 0)
-                s_red[d][wid] = pd;
+                s_red[d][wid] = (double)part.hi + (double)part.lo;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
