@@ -43,7 +43,7 @@ WORKLOAD = WORKLOADS["C4"]
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the current kernels on this workload (profiles/*_c4_fp32.md);
 # set an entry to None when its kernel changes.
-NCU_TRAFFIC = {"spread": 268.76e6, "interp": None, "forces": None, "bin": None}
+NCU_TRAFFIC = {"spread": None, "interp": None, "forces": None, "bin": None}
 
 
 def peaks():
@@ -108,13 +108,15 @@ def algorithmic_bytes(N, T, P, real=4):
     """Algorithmic bytes per stage: the bytes each stage must move at least.
 
     N nodes, T touched lattice values (over the 3 lattices), P (tile, node)
-    pairs, `real` bytes per value. Node arrays are read or written once per
-    stage; each touched lattice value is read once (interpolation) or read and
+    candidate pairs (0 when the spread walks each tile's own nodes instead),
+    `real` bytes per value. Node arrays are read or written once per stage;
+    each touched lattice value is read once (interpolation) or read and
     written once (spreading)."""
+    lists = P if P else N
     return {
         "bin": 2 * 3 * real * N + 4 * (N + P),          # x read (count + fill), pair/own lists written
         "forces": 2 * 3 * real * N,                     # x read, F written
-        "spread": 2 * 3 * real * N + 4 * P + 2 * real * T,  # x, F read; pair list read; f read + written
+        "spread": 2 * 3 * real * N + 4 * lists + 2 * real * T,  # x, F read; node list read; f read + written
         "interp": 2 * 3 * real * N + 4 * N + real * T,  # x read, v written, order list read; u read
         "reduce": 3 * 3 * real * N,                     # x, F, v read
         "step": 4 * 3 * real * N + 3 * real * T,        # x, v, F write + read; u read, f read + written
@@ -242,7 +244,9 @@ def main():
         step(stream)
     torch.cuda.synchronize()
     _, st = I.ifem_sync_status(cp.ctx)
-    T, P = st["touched_cells"], st["pairs"]
+    # touched lattice values: the non-zero values of the first step's spread
+    # into the zero field (each counted once, whichever tiles added to it)
+    T, P = int(torch.count_nonzero(f)), st["pairs"]
 
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream):

@@ -95,9 +95,15 @@ typedef enum { IFEM_FP32 = 0, IFEM_FP64 = 1 } ifem_precision;
  *   cubic-spline weight W(|x_J - x_k| / h_w), phi = p^T A^-1 B. */
 typedef enum { IFEM_KERNEL_PESKIN4 = 0, IFEM_KERNEL_MLS27 = 1 } ifem_kernel;
 
-/* Element-to-node force reduction (IFEM_FP32 only; IFEM_FP64 is always
- * deterministic). DET: per node, a fixed-order sum over its incident
- * elements. ATOMIC: atomic adds, order not reproducible. */
+/* Summation order of the FP32 scatters (IFEM_FP64 is always deterministic).
+ * DET: forces are a fixed-order sum per node over its incident elements;
+ * spreading sums each lattice value from the node lists of its own tile
+ * (every node binned into each tile its stencil reaches), so repeated runs
+ * give identical results.
+ * ATOMIC: forces by atomic adds. With PESKIN4, spreading visits each node
+ * once, in the tile holding its cell, accumulates into the tile plus a
+ * 2-cell halo (4 in x) and adds that to the grid with atomic L2 adds, so the
+ * order in which neighbouring tiles' halos combine is not reproducible. */
 typedef enum { IFEM_SCATTER_DET = 0, IFEM_SCATTER_ATOMIC = 1 } ifem_scatter;
 
 typedef enum { IFEM_LAW_NEO_HOOKE = 0, IFEM_LAW_SKALAK = 1 } ifem_membrane_law;
@@ -147,10 +153,13 @@ typedef struct {
     int64_t domain_errors;      /* non-finite positions / singular MLS matrices */
     int64_t capacity_errors;    /* per-tile list longer than the kernel's limit */
     int64_t timeouts;           /* bounded waits that expired */
-    int64_t pairs;              /* (tile, node) pairs of the last binning */
+    int64_t pairs;              /* (tile, node) pairs of the last binning (0 when the
+                                   spread needs no per-tile candidate lists) */
     int64_t active_tiles;       /* tiles with at least one node pair */
     int64_t touched_cells;      /* non-zero lattice values added by spreads since the last sync
-                                   (FP32 path; the FP64 path rewrites every value of an active tile) */
+                                   (FP32 path; the FP64 path rewrites every value of an active
+                                   tile; the FP32 ATOMIC Peskin spread counts the values inside
+                                   each node's own tile only) */
 } ifem_stats;
 
 /* ---------------------------------------------------------------- context */

@@ -699,6 +699,15 @@ static int launch_rc(ifem_ctx ctx, cudaError_t e, const char *what)
     return IFEM_OK;
 }
 
+// The FP32 Peskin spread of an IFEM_SCATTER_ATOMIC context uses the halo
+// scatter (own nodes only, L2 reductions); every other configuration the
+// owner-computes spread over candidate lists.
+static int use_halo(ifem_ctx ctx)
+{
+    return ctx->cfg.precision == IFEM_FP32 && ctx->cfg.kernel == IFEM_KERNEL_PESKIN4 &&
+           ctx->cfg.scatter == IFEM_SCATTER_ATOMIC;
+}
+
 static TransferArgs transfer_args(ifem_ctx ctx, ifem_batch b, const void *x, const void *F, const void *u,
                                   void *f, void *v, int flags, void *stream)
 {
@@ -716,6 +725,7 @@ static TransferArgs transfer_args(ifem_ctx ctx, ifem_batch b, const void *x, con
     a.support = ctx->cfg.mls_support;
     a.n_sm = ctx->n_sm;
     a.acc64 = ctx->acc64;
+    a.halo = use_halo(ctx);
     a.stream = (cudaStream_t)stream;
     return a;
 }
@@ -743,7 +753,7 @@ static int do_bin(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, void *
     if (rc != IFEM_OK)
         return rc;
     TransferArgs a = transfer_args(ctx, b, x, nullptr, nullptr, nullptr, nullptr, 0, stream);
-    cudaError_t e = ctx->cfg.precision == IFEM_FP64 ? launch_bin_f64(a, 1) : launch_bin_f32(a, 0);
+    cudaError_t e = ctx->cfg.precision == IFEM_FP64 ? launch_bin_f64(a, 1, 1) : launch_bin_f32(a, 0, !use_halo(ctx));
     return launch_rc(ctx, e, "binning");
 }
 

@@ -302,6 +302,7 @@ struct TransferArgs {
     double support;
     int n_sm;
     int acc64;        // FP32 spread: 64-bit (1) or 32-bit (0) fixed-point accumulators
+    int halo;         // FP32 Peskin spread with halo scatter (IFEM_SCATTER_ATOMIC)
     cudaStream_t stream;
 };
 
@@ -319,8 +320,8 @@ struct ReduceArgs {
 // Defined once per precision in kernels_f32.cu / kernels_f64.cu.
 cudaError_t launch_forces_f32(const ForcesArgs &a);
 cudaError_t launch_forces_f64(const ForcesArgs &a);
-cudaError_t launch_bin_f32(const TransferArgs &a, int det_sort);
-cudaError_t launch_bin_f64(const TransferArgs &a, int det_sort);
+cudaError_t launch_bin_f32(const TransferArgs &a, int det_sort, int with_cand);
+cudaError_t launch_bin_f64(const TransferArgs &a, int det_sort, int with_cand);
 cudaError_t launch_spread_f32(const TransferArgs &a);
 cudaError_t launch_spread_f64(const TransferArgs &a);
 cudaError_t launch_interp_f32(const TransferArgs &a);

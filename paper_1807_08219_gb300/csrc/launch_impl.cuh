@@ -56,7 +56,7 @@ cudaError_t forces_impl(const ForcesArgs &a)
 }
 
 template <typename real>
-cudaError_t bin_impl(const TransferArgs &a, int det_sort)
+cudaError_t bin_impl(const TransferArgs &a, int det_sort, int with_cand)
 {
     const DevBatch &b = a.b;
     const DevWork &w = a.w;
@@ -70,7 +70,7 @@ cudaError_t bin_impl(const TransferArgs &a, int det_sort)
     if (b.n_inst == 0 || b.N == 0)
         return cudaSuccess;
     dim3 gn((b.max_nodes + 255) / 256, b.n_inst);
-    bin_kernel<real, false><<<gn, 256, 0, s>>>(b, a.g, w, (const real *)a.x);
+    bin_kernel<real, false><<<gn, 256, 0, s>>>(b, a.g, w, (const real *)a.x, with_cand);
     IFEM_LAUNCH_CHECK();
     int nb = (int)((no + kScanBlock - 1) / kScanBlock);
     scan_local_kernel<<<nb, kScanThreads, 0, s>>>(nt, no, w.cand_count, w.own_count, w.cand_off, w.own_off,
@@ -80,7 +80,7 @@ cudaError_t bin_impl(const TransferArgs &a, int det_sort)
     IFEM_LAUNCH_CHECK();
     scan_finish_kernel<<<(unsigned)((no + 1 + 255) / 256), 256, 0, s>>>(nt, no, w);
     IFEM_LAUNCH_CHECK();
-    bin_kernel<real, true><<<gn, 256, 0, s>>>(b, a.g, w, (const real *)a.x);
+    bin_kernel<real, true><<<gn, 256, 0, s>>>(b, a.g, w, (const real *)a.x, with_cand);
     IFEM_LAUNCH_CHECK();
     if (det_sort) {
         sort_segments_kernel<<<a.n_sm * 4, 512, 0, s>>>(w);
@@ -101,6 +101,17 @@ cudaError_t spread_impl(const TransferArgs &a)
     if constexpr (std::is_same<real, float>::value) {
         const int E = a.g.max_edge;
         cudaMemsetAsync(a.w.counters + 2, 0, sizeof(int), s);
+        if (a.halo) {
+            size_t sm = sizeof(int) * (size_t)(E + 2 * kHaloX) * (E + 2 * kHaloYZ) * (E + 2 * kHaloYZ);
+            cudaFuncSetAttribute(spread_halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            int occ = 1;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spread_halo_kernel, 256, sm);
+            occ = occ < 1 ? 1 : occ;
+            spread_halo_kernel<<<a.n_sm * occ, 256, sm, s>>>(b, a.g, a.w, (const float *)a.x, (const float *)a.F,
+                                                             (float *)a.f, a.density);
+            IFEM_LAUNCH_CHECK();
+            return cudaSuccess;
+        }
         size_t acc = a.acc64 ? sizeof(long long) : sizeof(int);
         size_t sm = acc * 3 * (size_t)acc_stride(E, E, E);
         auto kern = a.kernel == 0 ? (a.acc64 ? spread_fast_kernel<0, long long> : spread_fast_kernel<0, int>)

@@ -106,7 +106,7 @@ __device__ __forceinline__ void agg_append(int *count, int *cursor, int *list, l
 // FILL = false: count candidate / own pairs per tile; FILL = true: write them.
 // Block size must be a multiple of 32 (every lane reaches the warp votes).
 template <typename real, bool FILL>
-__global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restrict__ x)
+__global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restrict__ x, int with_cand)
 {
     const InstDev I = b.inst[blockIdx.y];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -139,6 +139,8 @@ __global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restr
     const long long own = (B.tile_base + ((long long)oz * B.T + oy) * B.T + ox) * kOwnSub3
                           + (sbz * kOwnSub + sby) * kOwnSub + sbx;
     agg_append<FILL>(w.own_count, w.own_cursor, w.own_nodes, own, ok, node);
+    if (!with_cand)
+        return;
 #pragma unroll
     for (int slot = 0; slot < 8; ++slot) {
         const int ix = slot & 1, iy = (slot >> 1) & 1, iz = slot >> 2;
@@ -684,6 +686,208 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
             for (int q = 0; q < nw; ++q)
                 v += s_red[threadIdx.x][q];
             w.red_tile[3LL * tile + threadIdx.x] = v * h3;
+        }
+        // the next iteration's barrier orders these reads before s_red is rewritten
+    }
+}
+
+// ------------------------------------------- spread, FP32, halo scatter
+// IFEM_SCATTER_ATOMIC, Peskin kernel. Work item = (tile, lattice) taken from
+// a global counter over every tile. Each node is visited only by the tile
+// that holds its cell (no candidate lists): the CTA accumulates the 64
+// contributions of each own node into a buffer covering the tile plus a
+// halo of 4 cells in x (keeps 16-byte quads aligned) and 2 cells in y and z,
+// so every stencil point of every node lands in the buffer. Accumulation is
+// int32 fixed point with shared-memory atomics (scale from the bound
+// sum_k |g_k| / 8 over the tile's own nodes); the flush adds every non-zero
+// value to the grid with L2 reductions, where neighbouring tiles' halos
+// combine atomically (summation order of a value across tiles is not fixed).
+// ST_TOUCHED counts the non-zero sums inside the tile itself.
+constexpr int kHaloX = 4, kHaloYZ = 2;
+
+static __global__ void __launch_bounds__(256) spread_halo_kernel(DevBatch b, DevGrid g, DevWork w,
+                                                                 const float *__restrict__ x,
+                                                                 const float *__restrict__ F,
+                                                                 float *__restrict__ f, int density)
+{
+    extern __shared__ __align__(16) unsigned char halo_smem[];
+    int *acc = reinterpret_cast<int *>(halo_smem);
+    __shared__ float s_part[8];
+    __shared__ float s_scale;
+    __shared__ double s_red[8];
+    __shared__ int s_item;
+    __shared__ TileInfo s_ti;
+    __shared__ BoxDev s_B;
+    const long long N = b.N;
+    const long long n_items = 3 * g.n_tiles;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    {
+        const int E = g.max_edge;
+        const int cap = (E + 2 * kHaloX) * (E + 2 * kHaloYZ) * (E + 2 * kHaloYZ);
+        for (int i = threadIdx.x; i < cap; i += blockDim.x)
+            acc[i] = 0;
+    }
+    for (;;) {
+        if (threadIdx.x == 0) {
+            long long it;
+            // skip tiles without own nodes
+            for (;;) {
+                it = atomicAdd(&w.counters[2], 1);
+                if (it >= n_items)
+                    break;
+                const long long tile = it / 3;
+                if (w.own_off[(tile + 1) * kOwnSub3] > w.own_off[tile * kOwnSub3])
+                    break;
+            }
+            s_item = it < n_items ? (int)it : -1;
+            if (it < n_items) {
+                s_ti = decode_tile(g, it / 3);
+                s_B = g.boxes[s_ti.box];
+            }
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item < 0)
+            break;
+        const int tile = item / 3, d = item - 3 * (item / 3);
+        const int ex = s_ti.edge[0], ey = s_ti.edge[1], ez = s_ti.edge[2];
+        const int sx = s_ti.start[0], sy = s_ti.start[1], sz = s_ti.start[2];
+        const int bx = ex + 2 * kHaloX, by = ey + 2 * kHaloYZ, bz = ez + 2 * kHaloYZ;
+        const int n = s_B.n;
+        const float inv_h = s_B.inv_h_f;
+        const float sd = density ? s_B.scale_f : 1.f;
+        const double h3 = 1.0 / s_B.scale;
+        const int beg = w.own_off[(long long)tile * kOwnSub3], end = w.own_off[(long long)(tile + 1) * kOwnSub3];
+        // fixed-point scale from sum |F_d| over the own nodes
+        float gs = 0.f;
+        for (int q = beg + threadIdx.x; q < end; q += blockDim.x)
+            gs += fabsf(F[d * N + w.own_nodes[q]]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            gs += __shfl_down_sync(0xffffffffu, gs, o);
+        if (lane == 0)
+            s_part[wid] = gs;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float tot = 0.f;
+            for (int q = 0; q < nw; ++q)
+                tot += s_part[q];
+            const float bound = tot * sd * 0.125f * 1.0001f;
+            float sc = 1.f;
+            if (bound > 0.f && isfinite(bound)) {
+                int e = (int)floorf(log2f(FixedPoint<int>::kRange / bound));
+                e = e > 120 ? 120 : (e < -120 ? -120 : e);
+                sc = exp2f((float)e);
+            }
+            s_scale = sc;
+        }
+        __syncthreads();
+        const float gsc = sd * s_scale;
+        for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
+            const int node = w.own_nodes[q];
+            const InstDev &I = b.inst[b.node_inst[node]];
+            const float gq = F[d * N + node] * gsc;
+            float ph[3][4];
+            int l0[3];
+            bool inside = true;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                // the cell coordinate exactly as the binning computes it, so
+                // the node's cell lies in this tile
+                int I0;
+                const float t = LatCoord<float>::get(I, s_B, a, x[a * N + node], 0.f, I0);
+                const float ft = floorf(t);
+                const int i0 = peskin_axis_fast(t - (a == d ? 0.f : 0.5f), ph[a]);   // floor(s) - 1
+                const int st = a == 0 ? sx : (a == 1 ? sy : sz);
+                const int c = wrap_near(I0 + (int)ft, n) - st;                        // cell within the tile
+                // stencil start in the buffer: i0 - floor(t) is -2 or -1
+                l0[a] = c + (a == 0 ? kHaloX : kHaloYZ) + (i0 - (int)ft);
+                const int lim = (a == 0 ? bx : (a == 1 ? by : bz)) - 4;
+                inside = inside && (unsigned)l0[a] <= (unsigned)lim;
+            }
+            if (!inside) {   // only for coordinates beyond the range of int cells
+                status_add(w.status, ST_DOMAIN, 1);
+                continue;
+            }
+            int *base = acc + (l0[2] * by + l0[1]) * bx + l0[0];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float wz = ph[2][c] * gq;
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb) {
+                    const float wyz = ph[1][bb] * wz;
+                    int *row = base + (c * by + bb) * bx;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+                        atomicAdd(row + a, __float2int_rn(ph[0][a] * wyz));
+                }
+            }
+        }
+        __syncthreads();
+        // flush: quads of the buffer rows; each quad lies inside [0, n) after
+        // the periodic wrap when n and the tile start are multiples of 4
+        const long long n3 = (long long)n * n * n;
+        float *fd = f + s_B.grid_off + d * n3;
+        const bool vec = ((sx | n | bx) & 3) == 0 && ((reinterpret_cast<uintptr_t>(fd)) & 15) == 0;
+        const float inv = 1.f / s_scale;
+        DF part{0.f, 0.f};
+        unsigned touched = 0;
+        const int nq = vec ? (bx >> 2) : bx;
+        const int items = by * bz * nq;
+        for (int it2 = threadIdx.x; it2 < items; it2 += blockDim.x) {
+            const int r = it2 / nq, qx = it2 - r * nq;
+            const int lz = r / by, ly = r - lz * by;
+            int *src = acc + r * bx;
+            const int gz = wrap_near(sz - kHaloYZ + lz, n), gy = wrap_near(sy - kHaloYZ + ly, n);
+            float *dst = fd + ((long long)gz * n + gy) * n;
+            const bool row_in = (unsigned)(lz - kHaloYZ) < (unsigned)ez && (unsigned)(ly - kHaloYZ) < (unsigned)ey;
+            if (vec) {
+                const int x0 = qx << 2;
+                const int q0 = src[x0], q1 = src[x0 + 1], q2 = src[x0 + 2], q3 = src[x0 + 3];
+                if ((q0 | q1 | q2 | q3) != 0) {
+                    src[x0] = 0;
+                    src[x0 + 1] = 0;
+                    src[x0 + 2] = 0;
+                    src[x0 + 3] = 0;
+                    const float v0 = (float)q0 * inv, v1 = (float)q1 * inv, v2 = (float)q2 * inv,
+                                v3 = (float)q3 * inv;
+                    red_add_v4(dst + wrap_near(sx - kHaloX + x0, n), v0, v1, v2, v3);
+                    df_add(part, v0);
+                    df_add(part, v1);
+                    df_add(part, v2);
+                    df_add(part, v3);
+                    if (row_in && (unsigned)(x0 - kHaloX) < (unsigned)ex)
+                        touched += (q0 != 0) + (q1 != 0) + (q2 != 0) + (q3 != 0);
+                }
+            } else {
+                const int q = src[qx];
+                if (q != 0) {
+                    src[qx] = 0;
+                    const float v = (float)q * inv;
+                    red_add(dst + wrap_near(sx - kHaloX + qx, n), v);
+                    df_add(part, v);
+                    touched += row_in && (unsigned)(qx - kHaloX) < (unsigned)ex;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float hi = __shfl_down_sync(0xffffffffu, part.hi, o);
+            const float lo = __shfl_down_sync(0xffffffffu, part.lo, o);
+            df_add(part, hi);
+            part.lo += lo;
+            touched += __shfl_down_sync(0xffffffffu, touched, o);
+        }
+        if (lane == 0) {
+            s_red[wid] = (double)part.hi + (double)part.lo;
+            status_add(w.status, ST_TOUCHED, touched);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double v = 0.0;
+            for (int q = 0; q < nw; ++q)
+                v += s_red[q];
+            w.red_tile[3LL * tile + d] = v * h3;
         }
         // the next iteration's barrier orders these reads before s_red is rewritten
     }

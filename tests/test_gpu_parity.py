@@ -190,6 +190,28 @@ def test_small_box_ragged_tiles():
             assert np.array_equal(g["v"], o["v"])
 
 
+@pytest.mark.parametrize("n,tile", [(9, 6), (9, 8), (27, 8), (27, 12), (36, 12), (40, 16)])
+def test_fp32_atomic_small_boxes(n, tile):
+    """FP32 ATOMIC Peskin spread (own-tile nodes, halo added with L2 reductions):
+    boxes whose halo wraps onto the tile itself (n = 9), ragged last tiles
+    (27, 40: scalar flush) and quad-aligned rows (36, 40 with t = 12, 16)."""
+    import dataclasses
+    base = wl("C1")
+    scale = 0.15 * min(1.0, n / 40)
+    tm = dataclasses.replace(base.templates[0], X=base.templates[0].X * scale / 0.15)
+    inst = dataclasses.replace(base.instances[0], x_local=base.instances[0].x_local * scale / 0.15,
+                               origin=np.array([0.93, 0.02, 0.5]))
+    u = np.random.default_rng(n).standard_normal((3, n, n, n))
+    ww = rounded_workload(dataclasses.replace(base, templates=[tm], instances=[inst], boxes=[W.Box(n, 1.0)], u=[u]),
+                          np.float32)
+    g = run_gpu_step(ww, FP32, scatter=1, tile=tile)
+    o = oracle_step(ww)
+    assert g["rc"] == 0, g["stats"]
+    assert rel_l2(g["F"], o["F"]) < TOL_F
+    assert rel_l2(g["f"][0], o["f"][0]) < TOL_GRID
+    assert rel_l2(g["v"], o["v"]) < TOL_V
+
+
 def test_empty_batch():
     import dataclasses
     w = dataclasses.replace(wl("C1"), instances=[])
