@@ -146,6 +146,18 @@ __host__ __device__ inline int tiles_per_axis(int n, int t)
     return T;
 }
 
+// Reductions into shared memory addressed by 32-bit shared-window offsets
+// (no generic-to-shared address check per access).
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void red_shared_add(unsigned a, int v)
+{
+    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_shared_add(unsigned a, float v)
+{
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+
 __device__ inline void status_add(unsigned long long *st, int w, unsigned long long v)
 {
     if (v)

@@ -598,6 +598,7 @@ static __global__ void __launch_bounds__(512, 2) forces_fused_f32_kernel(DevBatc
     float *xs = sm;               // [3][nn]
     float *Fs = sm + 3 * nn;      // [3][nn]
     float *kHs = sm + 6 * nn;     // [nn]
+    const unsigned sF = smem_u32(Fs);
     for (int k = threadIdx.x; k < nn; k += blockDim.x) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -624,7 +625,7 @@ static __global__ void __launch_bounds__(512, 2) forces_fused_f32_kernel(DevBatc
             for (int c = 0; c < 3; ++c)
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
-                    atomicAdd(&Fs[a * nn + v[c]], f[c][a]);
+                    red_shared_add(sF + 4u * (unsigned)(a * nn + v[c]), f[c][a]);
         } else {
             int v[4];
             float p[4][3], f[4][3];
@@ -642,7 +643,7 @@ static __global__ void __launch_bounds__(512, 2) forces_fused_f32_kernel(DevBatc
             for (int c = 0; c < 4; ++c)
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
-                    atomicAdd(&Fs[a * nn + v[c]], f[c][a]);
+                    red_shared_add(sF + 4u * (unsigned)(a * nn + v[c]), f[c][a]);
         }
     }
     if (T.kind == 0 && T.kb != 0.0) {
@@ -660,7 +661,7 @@ static __global__ void __launch_bounds__(512, 2) forces_fused_f32_kernel(DevBatc
             const float mag = 2.f * kb * (2.f * dh * (kH * kH - kG + kH0 * kH)) * A;
 #pragma unroll
             for (int a = 0; a < 3; ++a)
-                atomicAdd(&Fs[a * nn + k], mag * n[a]);
+                red_shared_add(sF + 4u * (unsigned)(a * nn + k), mag * n[a]);
         }
         __syncthreads();
         for (int k = threadIdx.x; k < nn; k += blockDim.x) {
@@ -682,7 +683,7 @@ static __global__ void __launch_bounds__(512, 2) forces_fused_f32_kernel(DevBatc
             const float s = kb * lap * rsqrtf(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
 #pragma unroll
             for (int a = 0; a < 3; ++a)
-                atomicAdd(&Fs[a * nn + k], s * nrm[a]);
+                red_shared_add(sF + 4u * (unsigned)(a * nn + k), s * nrm[a]);
         }
     }
     __syncthreads();

@@ -102,7 +102,7 @@ cudaError_t spread_impl(const TransferArgs &a)
         const int E = a.g.max_edge;
         cudaMemsetAsync(a.w.counters + 2, 0, sizeof(int), s);
         if (a.halo) {
-            size_t sm = sizeof(int) * (size_t)(E + 2 * kHaloX) * (E + 2 * kHaloYZ) * (E + 2 * kHaloYZ);
+            size_t sm = sizeof(int) * (size_t)halo_ints(E);
             cudaFuncSetAttribute(spread_halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             int occ = 1;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spread_halo_kernel, 256, sm);

@@ -705,6 +705,17 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
 // ST_TOUCHED counts the non-zero sums inside the tile itself.
 constexpr int kHaloX = 4, kHaloYZ = 2;
 
+// Buffer pitches: the row pitch is 8 mod 16 and the plane pitch 4 mod 8, so
+// the 4 x 4 x 4 cells around a group of neighbouring nodes fall on all 32
+// banks, two cells per bank; both stay multiples of 4 for 16-byte rows.
+__host__ __device__ inline int halo_px(int bx) { return bx + (24 - bx % 16) % 16; }
+__host__ __device__ inline int halo_pp(int by, int px) { return by * px + 4; }
+__host__ __device__ inline int halo_ints(int E)
+{
+    const int px = halo_px(E + 2 * kHaloX);
+    return halo_pp(E + 2 * kHaloYZ, px) * (E + 2 * kHaloYZ);
+}
+
 static __global__ void __launch_bounds__(256) spread_halo_kernel(DevBatch b, DevGrid g, DevWork w,
                                                                  const float *__restrict__ x,
                                                                  const float *__restrict__ F,
@@ -712,21 +723,18 @@ static __global__ void __launch_bounds__(256) spread_halo_kernel(DevBatch b, Dev
 {
     extern __shared__ __align__(16) unsigned char halo_smem[];
     int *acc = reinterpret_cast<int *>(halo_smem);
+    const unsigned sacc = smem_u32(acc);
     __shared__ float s_part[8];
     __shared__ float s_scale;
-    __shared__ double s_red[8];
+    __shared__ long long s_red[8];
     __shared__ int s_item;
     __shared__ TileInfo s_ti;
     __shared__ BoxDev s_B;
     const long long N = b.N;
     const long long n_items = 3 * g.n_tiles;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    {
-        const int E = g.max_edge;
-        const int cap = (E + 2 * kHaloX) * (E + 2 * kHaloYZ) * (E + 2 * kHaloYZ);
-        for (int i = threadIdx.x; i < cap; i += blockDim.x)
-            acc[i] = 0;
-    }
+    for (int i = threadIdx.x; i < halo_ints(g.max_edge); i += blockDim.x)
+        acc[i] = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             long long it;
@@ -753,10 +761,9 @@ static __global__ void __launch_bounds__(256) spread_halo_kernel(DevBatch b, Dev
         const int ex = s_ti.edge[0], ey = s_ti.edge[1], ez = s_ti.edge[2];
         const int sx = s_ti.start[0], sy = s_ti.start[1], sz = s_ti.start[2];
         const int bx = ex + 2 * kHaloX, by = ey + 2 * kHaloYZ, bz = ez + 2 * kHaloYZ;
+        const int px = halo_px(bx), pp = halo_pp(by, px);
         const int n = s_B.n;
-        const float inv_h = s_B.inv_h_f;
         const float sd = density ? s_B.scale_f : 1.f;
-        const double h3 = 1.0 / s_B.scale;
         const int beg = w.own_off[(long long)tile * kOwnSub3], end = w.own_off[(long long)(tile + 1) * kOwnSub3];
         // fixed-point scale from sum |F_d| over the own nodes
         float gs = 0.f;
@@ -809,85 +816,95 @@ static __global__ void __launch_bounds__(256) spread_halo_kernel(DevBatch b, Dev
                 status_add(w.status, ST_DOMAIN, 1);
                 continue;
             }
-            int *base = acc + (l0[2] * by + l0[1]) * bx + l0[0];
+            const unsigned base = sacc + 4u * (unsigned)(l0[2] * pp + l0[1] * px + l0[0]);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const float wz = ph[2][c] * gq;
 #pragma unroll
                 for (int bb = 0; bb < 4; ++bb) {
                     const float wyz = ph[1][bb] * wz;
-                    int *row = base + (c * by + bb) * bx;
+                    const unsigned row = base + 4u * (unsigned)(c * pp + bb * px);
 #pragma unroll
                     for (int a = 0; a < 4; ++a)
-                        atomicAdd(row + a, __float2int_rn(ph[0][a] * wyz));
+                        red_shared_add(row + 4u * a, __float2int_rn(ph[0][a] * wyz));
                 }
             }
         }
         __syncthreads();
-        // flush: quads of the buffer rows; each quad lies inside [0, n) after
-        // the periodic wrap when n and the tile start are multiples of 4
+        // flush. Each warp takes groups of whole rows, a lane one quad (or one
+        // value when rows are not 16-byte aligned) at a fixed x; rows advance
+        // by a fixed (y, z) step, so no index is divided in the loop. Quads
+        // lie inside [0, n) after the periodic wrap when n and the tile start
+        // are multiples of 4.
         const long long n3 = (long long)n * n * n;
         float *fd = f + s_B.grid_off + d * n3;
         const bool vec = ((sx | n | bx) & 3) == 0 && ((reinterpret_cast<uintptr_t>(fd)) & 15) == 0;
         const float inv = 1.f / s_scale;
-        DF part{0.f, 0.f};
+        const int per = vec ? 4 : 1;
+        const int nq = bx / per;                        // quads (or values) per row
+        const int nql = nq <= 32 ? nq : 32;             // lanes per row
+        const int rpw = 32 / nql;                       // rows per warp step
+        const int lr = lane / nql, lq = lane - lr * nql;
+        long long qsum = 0;
         unsigned touched = 0;
-        const int nq = vec ? (bx >> 2) : bx;
-        const int items = by * bz * nq;
-        for (int it2 = threadIdx.x; it2 < items; it2 += blockDim.x) {
-            const int r = it2 / nq, qx = it2 - r * nq;
-            const int lz = r / by, ly = r - lz * by;
-            int *src = acc + r * bx;
-            const int gz = wrap_near(sz - kHaloYZ + lz, n), gy = wrap_near(sy - kHaloYZ + ly, n);
-            float *dst = fd + ((long long)gz * n + gy) * n;
-            const bool row_in = (unsigned)(lz - kHaloYZ) < (unsigned)ez && (unsigned)(ly - kHaloYZ) < (unsigned)ey;
-            if (vec) {
-                const int x0 = qx << 2;
-                const int q0 = src[x0], q1 = src[x0 + 1], q2 = src[x0 + 2], q3 = src[x0 + 3];
-                if ((q0 | q1 | q2 | q3) != 0) {
-                    src[x0] = 0;
-                    src[x0 + 1] = 0;
-                    src[x0 + 2] = 0;
-                    src[x0 + 3] = 0;
-                    const float v0 = (float)q0 * inv, v1 = (float)q1 * inv, v2 = (float)q2 * inv,
-                                v3 = (float)q3 * inv;
-                    red_add_v4(dst + wrap_near(sx - kHaloX + x0, n), v0, v1, v2, v3);
-                    df_add(part, v0);
-                    df_add(part, v1);
-                    df_add(part, v2);
-                    df_add(part, v3);
-                    if (row_in && (unsigned)(x0 - kHaloX) < (unsigned)ex)
-                        touched += (q0 != 0) + (q1 != 0) + (q2 != 0) + (q3 != 0);
+        if (lr < rpw) {
+            const int rstep = nw * rpw;
+            int r0 = wid * rpw + lr;
+            int lz = r0 / by, ly = r0 - lz * by;
+            const int dz = rstep / by, dy = rstep - dz * by;
+            for (; lz < bz;) {
+                const int gz = wrap_near(sz - kHaloYZ + lz, n), gy = wrap_near(sy - kHaloYZ + ly, n);
+                float *dst = fd + ((long long)gz * n + gy) * n;
+                int *src = acc + lz * pp + ly * px;
+                const bool row_in =
+                    (unsigned)(lz - kHaloYZ) < (unsigned)ez && (unsigned)(ly - kHaloYZ) < (unsigned)ey;
+                if (vec) {
+                    const int x0 = lq << 2;
+                    int4 *sp = reinterpret_cast<int4 *>(src + x0);
+                    const int4 qv = *sp;
+                    if ((qv.x | qv.y | qv.z | qv.w) != 0) {
+                        *sp = make_int4(0, 0, 0, 0);
+                        red_add_v4(dst + wrap_near(sx - kHaloX + x0, n), (float)qv.x * inv, (float)qv.y * inv,
+                                   (float)qv.z * inv, (float)qv.w * inv);
+                        qsum += (long long)qv.x + (long long)qv.y + (long long)qv.z + (long long)qv.w;
+                        if (row_in && (unsigned)(x0 - kHaloX) < (unsigned)ex)
+                            touched += (qv.x != 0) + (qv.y != 0) + (qv.z != 0) + (qv.w != 0);
+                    }
+                } else {
+                    for (int qx = lq; qx < bx; qx += nql) {
+                        const int q = src[qx];
+                        if (q != 0) {
+                            src[qx] = 0;
+                            red_add(dst + wrap_near(sx - kHaloX + qx, n), (float)q * inv);
+                            qsum += q;
+                            touched += row_in && (unsigned)(qx - kHaloX) < (unsigned)ex;
+                        }
+                    }
                 }
-            } else {
-                const int q = src[qx];
-                if (q != 0) {
-                    src[qx] = 0;
-                    const float v = (float)q * inv;
-                    red_add(dst + wrap_near(sx - kHaloX + qx, n), v);
-                    df_add(part, v);
-                    touched += row_in && (unsigned)(qx - kHaloX) < (unsigned)ex;
+                ly += dy;
+                lz += dz;
+                if (ly >= by) {
+                    ly -= by;
+                    ++lz;
                 }
             }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const float hi = __shfl_down_sync(0xffffffffu, part.hi, o);
-            const float lo = __shfl_down_sync(0xffffffffu, part.lo, o);
-            df_add(part, hi);
-            part.lo += lo;
+            qsum += __shfl_down_sync(0xffffffffu, qsum, o);
             touched += __shfl_down_sync(0xffffffffu, touched, o);
         }
         if (lane == 0) {
-            s_red[wid] = (double)part.hi + (double)part.lo;
+            s_red[wid] = qsum;
             status_add(w.status, ST_TOUCHED, touched);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double v = 0.0;
+            long long v = 0;
             for (int q = 0; q < nw; ++q)
                 v += s_red[q];
-            w.red_tile[3LL * tile + d] = v * h3;
+            // exact: |v| < 2^53, inv a power of two
+            w.red_tile[3LL * tile + d] = (double)v * (double)inv / s_B.scale;
         }
         // the next iteration's barrier orders these reads before s_red is rewritten
     }
