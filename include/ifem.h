@@ -179,7 +179,9 @@ int ifem_ctx_tile(ifem_ctx ctx);
 /* Stage durations of the last ifem_step_coupling call on a context created
  * with cfg.profile = 1, measured with CUDA events recorded on that call's
  * stream: ms[0] binning, ms[1] forces, ms[2] spread, ms[3] interpolation,
- * ms[4] reductions (milliseconds). Waits for the last recorded event.
+ * ms[4] reductions (milliseconds); where the step fuses interpolation into
+ * the spread (see ifem_step_coupling) ms[2] covers both and ms[3] is 0.
+ * Waits for the last recorded event.
  * IFEM_ERR_ARG if profiling is off or no step has run. */
 int ifem_stage_times(ifem_ctx ctx, double *ms);
 
@@ -279,7 +281,10 @@ int ifem_reduce(ifem_ctx ctx, ifem_batch b, const void *x, const void *F, const 
  * context owns, forked from `stream` with events and joined back into it
  * before the reductions (valid under CUDA-graph capture of `stream`); with
  * cfg.profile = 1 the stages run one after the other on `stream` instead, so
- * that ifem_stage_times can attribute them. */
+ * that ifem_stage_times can attribute them. With IFEM_FP32, IFEM_SCATTER_ATOMIC
+ * and IFEM_KERNEL_PESKIN4 the interpolation is fused into the spreading
+ * kernel (each node's stencil weights serve both transfers); results equal
+ * those of the separate calls up to FP32 rounding. */
 int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *u,
                        void *F, void *f, void *v, double *red, int flags, void *stream);
 

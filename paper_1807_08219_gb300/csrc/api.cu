@@ -161,6 +161,10 @@ extern "C" int ifem_stage_times(ifem_ctx ctx, double *ms)
         CK(cudaEventElapsedTime(&t, ctx->ev[i], ctx->ev[i + 1]));
         ms[i] = t;
     }
+    if (ctx->ev_fused) {
+        ms[2] += ms[3];
+        ms[3] = 0.0;
+    }
     return IFEM_OK;
 }
 
@@ -770,6 +774,20 @@ static int do_spread(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
     return launch_rc(ctx, e, "spread");
 }
 
+// Spreading with the interpolation of the same step fused into it (the
+// halo-scatter configuration only): one launch per step for both transfers.
+static int do_spread_interp(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *F, const void *u,
+                            void *f, void *v, int flags, void *stream)
+{
+    if (flags & IFEM_SPREAD_OVERWRITE) {
+        cudaError_t e = cudaMemsetAsync(f, 0, (size_t)g->total * real_size(ctx), (cudaStream_t)stream);
+        if (e != cudaSuccess)
+            return launch_rc(ctx, e, "spread overwrite");
+    }
+    TransferArgs a = transfer_args(ctx, b, x, F, u, f, v, flags, stream);
+    return launch_rc(ctx, launch_spread_f32(a), "spread + interpolate");
+}
+
 static int do_interp(ifem_ctx ctx, ifem_batch b, const void *u, const void *x, void *v, void *stream)
 {
     TransferArgs a = transfer_args(ctx, b, x, nullptr, u, nullptr, v, 0, stream);
@@ -880,11 +898,18 @@ extern "C" int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const
         if ((rc = do_forces(ctx, b, x, F, nullptr, 0, stream)) != IFEM_OK)
             return rc;
         mark(ctx, 2, stream);
-        if ((rc = do_spread(ctx, b, g, x, F, f, flags, stream)) != IFEM_OK)
-            return rc;
-        mark(ctx, 3, stream);
-        if ((rc = do_interp(ctx, b, u, x, v, stream)) != IFEM_OK)
-            return rc;
+        ctx->ev_fused = use_halo(ctx);
+        if (ctx->ev_fused) {
+            if ((rc = do_spread_interp(ctx, b, g, x, F, u, f, v, flags, stream)) != IFEM_OK)
+                return rc;
+            mark(ctx, 3, stream);
+        } else {
+            if ((rc = do_spread(ctx, b, g, x, F, f, flags, stream)) != IFEM_OK)
+                return rc;
+            mark(ctx, 3, stream);
+            if ((rc = do_interp(ctx, b, u, x, v, stream)) != IFEM_OK)
+                return rc;
+        }
         mark(ctx, 4, stream);
         if (red && (rc = do_reduce(ctx, b, x, F, v, red, stream)) != IFEM_OK)
             return rc;
@@ -897,6 +922,8 @@ extern "C" int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const
     //   s:    bin ----------- wait(forces) spread  wait(interp) reduce
     //   aux0: forces -------/
     //   aux1:       wait(bin) interp -------------/
+    // (with the fused spread + interpolation the aux1 branch is absent)
+    const bool fused = use_halo(ctx) != 0;
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = ws_ensure(ctx, b, g, ctx->tile)) != IFEM_OK)
         return rc;
@@ -911,20 +938,27 @@ extern "C" int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const
         return launch_rc(ctx, e, "step_coupling fork");
     if ((rc = do_bin(ctx, b, g, x, stream)) != IFEM_OK)
         return rc;
-    if ((e = cudaEventRecord(ctx->fork[2], s)) == cudaSuccess)
-        e = cudaStreamWaitEvent(ctx->aux[1], ctx->fork[2], 0);
-    if (e != cudaSuccess)
-        return launch_rc(ctx, e, "step_coupling fork");
-    if ((rc = do_interp(ctx, b, u, x, v, ctx->aux[1])) != IFEM_OK)
-        return rc;
-    if ((e = cudaEventRecord(ctx->fork[3], ctx->aux[1])) == cudaSuccess)
-        e = cudaStreamWaitEvent(s, ctx->fork[1], 0);
-    if (e != cudaSuccess)
+    if (!fused) {
+        if ((e = cudaEventRecord(ctx->fork[2], s)) == cudaSuccess)
+            e = cudaStreamWaitEvent(ctx->aux[1], ctx->fork[2], 0);
+        if (e != cudaSuccess)
+            return launch_rc(ctx, e, "step_coupling fork");
+        if ((rc = do_interp(ctx, b, u, x, v, ctx->aux[1])) != IFEM_OK)
+            return rc;
+        if ((e = cudaEventRecord(ctx->fork[3], ctx->aux[1])) != cudaSuccess)
+            return launch_rc(ctx, e, "step_coupling fork");
+    }
+    if ((e = cudaStreamWaitEvent(s, ctx->fork[1], 0)) != cudaSuccess)
         return launch_rc(ctx, e, "step_coupling join");
-    if ((rc = do_spread(ctx, b, g, x, F, f, flags, stream)) != IFEM_OK)
-        return rc;
-    if ((e = cudaStreamWaitEvent(s, ctx->fork[3], 0)) != cudaSuccess)
-        return launch_rc(ctx, e, "step_coupling join");
+    if (fused) {
+        if ((rc = do_spread_interp(ctx, b, g, x, F, u, f, v, flags, stream)) != IFEM_OK)
+            return rc;
+    } else {
+        if ((rc = do_spread(ctx, b, g, x, F, f, flags, stream)) != IFEM_OK)
+            return rc;
+        if ((e = cudaStreamWaitEvent(s, ctx->fork[3], 0)) != cudaSuccess)
+            return launch_rc(ctx, e, "step_coupling join");
+    }
     if (red && (rc = do_reduce(ctx, b, x, F, v, red, stream)) != IFEM_OK)
         return rc;
     return IFEM_OK;

@@ -21,6 +21,7 @@ struct ifem_ctx_s {
     cudaEvent_t ev[6] = {};
     int ev_ok = 0;
     int ev_recorded = 0;
+    int ev_fused = 0;   // the recorded step fused interpolation into the spread
     int acc64 = 0;
     int tuned = 0;
     cudaStream_t aux[2] = {};   // fork-join streams of ifem_step_coupling

@@ -102,13 +102,16 @@ cudaError_t spread_impl(const TransferArgs &a)
         const int E = a.g.max_edge;
         cudaMemsetAsync(a.w.counters + 2, 0, sizeof(int), s);
         if (a.halo) {
+            // with u and v given, interpolation is fused into the spread
+            const bool fused = a.u != nullptr && a.v != nullptr;
+            auto kern = fused ? spread_halo_kernel<true> : spread_halo_kernel<false>;
             size_t sm = sizeof(int) * (size_t)halo_ints(E);
-            cudaFuncSetAttribute(spread_halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             int occ = 1;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spread_halo_kernel, 256, sm);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, sm);
             occ = occ < 1 ? 1 : occ;
-            spread_halo_kernel<<<a.n_sm * occ, 256, sm, s>>>(b, a.g, a.w, (const float *)a.x, (const float *)a.F,
-                                                             (float *)a.f, a.density);
+            kern<<<a.n_sm * occ, 256, sm, s>>>(b, a.g, a.w, (const float *)a.x, (const float *)a.F, (float *)a.f,
+                                               a.density, (const float *)a.u, (float *)a.v);
             IFEM_LAUNCH_CHECK();
             return cudaSuccess;
         }

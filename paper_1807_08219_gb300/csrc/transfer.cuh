@@ -353,6 +353,22 @@ __device__ __forceinline__ void df_add(DF &x, float v)
     x.hi = s + t;
     x.lo = t - (x.hi - s);
 }
+// x += y for two float pairs, with both the high and the low sums made exact
+// by TwoSum before renormalising (relative error a few 2^-48).
+__device__ __forceinline__ void df_add_df(DF &x, DF y)
+{
+    const float s = x.hi + y.hi;
+    const float bs = s - x.hi;
+    float e = (x.hi - (s - bs)) + (y.hi - bs);
+    const float t = x.lo + y.lo;
+    const float bt = t - x.lo;
+    const float f = (x.lo - (t - bt)) + (y.lo - bt);
+    e += t;
+    const float h = s + e;
+    e = (e - (h - s)) + f;
+    x.hi = h + e;
+    x.lo = e - (x.hi - h);
+}
 __device__ __forceinline__ void df_add_prod(DF &x, float a, float b)
 {
     const float p = a * b;
@@ -716,10 +732,16 @@ __host__ __device__ inline int halo_ints(int E)
     return halo_pp(E + 2 * kHaloYZ, px) * (E + 2 * kHaloYZ);
 }
 
-static __global__ void __launch_bounds__(256) spread_halo_kernel(DevBatch b, DevGrid g, DevWork w,
-                                                                 const float *__restrict__ x,
-                                                                 const float *__restrict__ F,
-                                                                 float *__restrict__ f, int density)
+//
+// INTERP = true fuses the interpolation S of the same step: each (node,
+// lattice) unit also gathers u at the 64 stencil points with the unscaled
+// weights it has just computed, v_d = sum phi u_d (Algorithm step 4).
+template <bool INTERP>
+__global__ void __launch_bounds__(256) spread_halo_kernel(DevBatch b, DevGrid g, DevWork w,
+                                                          const float *__restrict__ x,
+                                                          const float *__restrict__ F, float *__restrict__ f,
+                                                          int density, const float *__restrict__ u,
+                                                          float *__restrict__ v)
 {
     extern __shared__ __align__(16) unsigned char halo_smem[];
     int *acc = reinterpret_cast<int *>(halo_smem);
@@ -817,16 +839,62 @@ static __global__ void __launch_bounds__(256) spread_halo_kernel(DevBatch b, Dev
                 continue;
             }
             const unsigned base = sacc + 4u * (unsigned)(l0[2] * pp + l0[1] * px + l0[0]);
+            if constexpr (INTERP) {
+                // grid indices of the stencil (the buffer origin is the tile
+                // start minus the halo); per z plane the 16 gathers are issued
+                // before that plane's shared-memory reductions
+                const float *ud = u + s_B.grid_off + (long long)d * n * n * n;
+                int gx[4], gy[4], gz[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float wz = ph[2][c] * gq;
+                for (int m = 0; m < 4; ++m) {
+                    gx[m] = wrap_near(sx - kHaloX + l0[0] + m, n);
+                    gy[m] = wrap_near(sy - kHaloYZ + l0[1] + m, n);
+                    gz[m] = wrap_near(sz - kHaloYZ + l0[2] + m, n);
+                }
+                float out = 0.f;
 #pragma unroll
-                for (int bb = 0; bb < 4; ++bb) {
-                    const float wyz = ph[1][bb] * wz;
-                    const unsigned row = base + 4u * (unsigned)(c * pp + bb * px);
+                for (int c = 0; c < 4; ++c) {
+                    float uv[4][4];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a)
-                        red_shared_add(row + 4u * a, __float2int_rn(ph[0][a] * wyz));
+                    for (int bb = 0; bb < 4; ++bb) {
+                        const float *row = ud + (gz[c] * n + gy[bb]) * n;
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+                            uv[bb][a] = __ldg(row + gx[a]);
+                    }
+                    const float wz = ph[2][c] * gq;
+#pragma unroll
+                    for (int bb = 0; bb < 4; ++bb) {
+                        const float wyz = ph[1][bb] * wz;
+                        const unsigned row = base + 4u * (unsigned)(c * pp + bb * px);
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+                            red_shared_add(row + 4u * a, __float2int_rn(ph[0][a] * wyz));
+                    }
+                    float accz = 0.f;
+#pragma unroll
+                    for (int bb = 0; bb < 4; ++bb) {
+                        float accy = ph[0][0] * uv[bb][0];
+#pragma unroll
+                        for (int a = 1; a < 4; ++a)
+                            accy += ph[0][a] * uv[bb][a];
+                        accz += ph[1][bb] * accy;
+                    }
+                    out += ph[2][c] * accz;
+                }
+                v[d * N + node] = out;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float wz = ph[2][c] * gq;
+#pragma unroll
+                    for (int bb = 0; bb < 4; ++bb) {
+                        const float wyz = ph[1][bb] * wz;
+                        const unsigned row = base + 4u * (unsigned)(c * pp + bb * px);
+#pragma unroll
+                        for (int a = 0; a < 4; ++a)
+                            red_shared_add(row + 4u * a, __float2int_rn(ph[0][a] * wyz));
+                    }
                 }
             }
         }
@@ -1348,9 +1416,20 @@ __global__ void __launch_bounds__(256) reduce_inst_kernel(DevBatch b, const real
             df_add_prod(q[8], xk[0], Fk[1]);
             df_add_prod(q[8], -xk[1], Fk[0]);
         }
+        // warp sums in float pairs; one FP64 conversion per warp and quantity
 #pragma unroll
-        for (int i = 0; i < 12; ++i)
-            p[i] = (double)q[i].hi + (double)q[i].lo;
+        for (int i = 0; i < 12; ++i) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const DF y{__shfl_down_sync(0xffffffffu, q[i].hi, o), __shfl_down_sync(0xffffffffu, q[i].lo, o)};
+                df_add_df(q[i], y);
+            }
+        }
+        if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+            for (int i = 0; i < 12; ++i)
+                sh[i][threadIdx.x >> 5] = (double)q[i].hi + (double)q[i].lo;
+        }
     } else {
 #pragma unroll
         for (int i = 0; i < 12; ++i)
@@ -1371,15 +1450,17 @@ __global__ void __launch_bounds__(256) reduce_inst_kernel(DevBatch b, const real
             p[8] += xk[0] * Fk[1] - xk[1] * Fk[0];
         }
     }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if constexpr (!std::is_same<real, float>::value) {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int q = 0; q < 12; ++q) {
-        double t = p[q];
+        for (int q = 0; q < 12; ++q) {
+            double t = p[q];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            t += __shfl_down_sync(0xffffffffu, t, o);
-        if (lane == 0)
-            sh[q][wid] = t;
+            for (int o = 16; o > 0; o >>= 1)
+                t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0)
+                sh[q][wid] = t;
+        }
     }
     __syncthreads();
     if (threadIdx.x < 12) {
