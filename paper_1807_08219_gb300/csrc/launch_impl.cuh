@@ -167,12 +167,9 @@ cudaError_t interp_impl(const TransferArgs &a)
 template <typename real>
 cudaError_t reduce_impl(const ReduceArgs &a)
 {
-    if (a.b.n_inst > 0) {
-        reduce_inst_kernel<real><<<a.b.n_inst, 256, 0, a.stream>>>(a.b, (const real *)a.x, (const real *)a.F,
-                                                                   (const real *)a.v, a.red);
-        IFEM_LAUNCH_CHECK();
-    }
-    reduce_box_kernel<<<a.g.n_boxes, 256, 0, a.stream>>>(a.g, a.w.red_tile, a.red + 12LL * a.b.n_inst);
+    const unsigned blocks = (unsigned)(a.b.n_inst + 3 * a.g.n_boxes);
+    reduce_kernel<real><<<blocks, kReduceThreads, 0, a.stream>>>(a.b, a.g, a.w.red_tile, (const real *)a.x,
+                                                               (const real *)a.F, (const real *)a.v, a.red);
     IFEM_LAUNCH_CHECK();
     return cudaSuccess;
 }

@@ -1378,21 +1378,46 @@ __device__ inline double block_sum(double v, double *sh)
     return r;
 }
 
-// One pass per instance: partial sums of x, F, v and x (x) F (about the
-// instance's local origin) per thread -- float pairs for FP32 inputs, FP64
-// for FP64 inputs -- then FP64 in a fixed warp/CTA tree.
-// Torque about the centroid: sum (x - c) x F = sum x x F - c x sum F.
+// One launch for all conservation sums. Blocks [0, n_inst): one instance
+// each -- partial sums of x, F, v and x (x) F (about the instance's local
+// origin) per thread, float pairs for FP32 inputs (FP64 for FP64 inputs),
+// then a fixed-order tree: FP32 partials are transposed through shared
+// memory so that each warp reduces one or two quantities in float pairs and
+// converts once to FP64. Torque about the centroid:
+// sum (x - c) x F = sum x x F - c x sum F.
+// Blocks [n_inst, n_inst + 3 n_boxes): box b, lattice d -- h^3 * sum of the
+// values the last spread added, from the per-tile FP64 partials in tile order.
+constexpr int kReduceThreads = 256;
+
 template <typename real>
-__global__ void __launch_bounds__(256) reduce_inst_kernel(DevBatch b, const real *__restrict__ x,
-                                                          const real *__restrict__ F,
-                                                          const real *__restrict__ v, double *__restrict__ red)
+__global__ void __launch_bounds__(kReduceThreads) reduce_kernel(DevBatch b, DevGrid g,
+                                                               const double *__restrict__ red_tile,
+                                                               const real *__restrict__ x,
+                                                               const real *__restrict__ F,
+                                                               const real *__restrict__ v, double *__restrict__ red)
 {
-    __shared__ double sh[12][8];
+    __shared__ double sh[kReduceThreads];
     __shared__ double tot[12];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (blockIdx.x >= b.n_inst) {
+        const int k = blockIdx.x - b.n_inst, bx = k / 3, d = k - 3 * bx;
+        const BoxDev B = g.boxes[bx];
+        const long long nt = (long long)B.T * B.T * B.T;
+        double s = 0.0;
+        for (long long t = threadIdx.x; t < nt; t += blockDim.x)
+            s += red_tile[3 * (B.tile_base + t) + d];
+        const double r = block_sum<kReduceThreads>(s, sh);
+        if (threadIdx.x == 0) {
+            double *o = red + 12LL * b.n_inst + 6LL * bx;
+            o[d] = r;
+            o[3 + d] = 0.0;
+        }
+        return;
+    }
     const InstDev I = b.inst[blockIdx.x];
     const long long N = b.N;
-    double p[12];
     if constexpr (std::is_same<real, float>::value) {
+        __shared__ float2 part[12][kReduceThreads];
         DF q[12];
 #pragma unroll
         for (int i = 0; i < 12; ++i)
@@ -1416,21 +1441,26 @@ __global__ void __launch_bounds__(256) reduce_inst_kernel(DevBatch b, const real
             df_add_prod(q[8], xk[0], Fk[1]);
             df_add_prod(q[8], -xk[1], Fk[0]);
         }
-        // warp sums in float pairs; one FP64 conversion per warp and quantity
 #pragma unroll
-        for (int i = 0; i < 12; ++i) {
+        for (int i = 0; i < 12; ++i)
+            part[i][threadIdx.x] = make_float2(q[i].hi, q[i].lo);
+        __syncthreads();
+        for (int i = wid; i < 12; i += nw) {
+            DF s{0.f, 0.f};
+            for (int k = lane; k < (int)blockDim.x; k += 32) {
+                const float2 e = part[i][k];
+                df_add_df(s, DF{e.x, e.y});
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const DF y{__shfl_down_sync(0xffffffffu, q[i].hi, o), __shfl_down_sync(0xffffffffu, q[i].lo, o)};
-                df_add_df(q[i], y);
+                const DF y{__shfl_down_sync(0xffffffffu, s.hi, o), __shfl_down_sync(0xffffffffu, s.lo, o)};
+                df_add_df(s, y);
             }
-        }
-        if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-            for (int i = 0; i < 12; ++i)
-                sh[i][threadIdx.x >> 5] = (double)q[i].hi + (double)q[i].lo;
+            if (lane == 0)
+                tot[i] = (double)s.hi + (double)s.lo;
         }
     } else {
+        double p[12];
 #pragma unroll
         for (int i = 0; i < 12; ++i)
             p[i] = 0.0;
@@ -1449,30 +1479,27 @@ __global__ void __launch_bounds__(256) reduce_inst_kernel(DevBatch b, const real
             p[7] += xk[2] * Fk[0] - xk[0] * Fk[2];
             p[8] += xk[0] * Fk[1] - xk[1] * Fk[0];
         }
-    }
-    if constexpr (!std::is_same<real, float>::value) {
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-        for (int q = 0; q < 12; ++q) {
-            double t = p[q];
+        for (int i = 0; i < 12; ++i) {
+            double t = p[i];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
                 t += __shfl_down_sync(0xffffffffu, t, o);
             if (lane == 0)
-                sh[q][wid] = t;
+                sh[i * 8 + wid] = t;
         }
-    }
-    __syncthreads();
-    if (threadIdx.x < 12) {
-        double t = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
-            t += sh[threadIdx.x][q];
-        tot[threadIdx.x] = t;
+        __syncthreads();
+        if (threadIdx.x < 12) {
+            double t = 0.0;
+            for (int k = 0; k < nw; ++k)
+                t += sh[threadIdx.x * 8 + k];
+            tot[threadIdx.x] = t;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double *o = red + 12LL * blockIdx.x;
-        double c[3] = {tot[0] / I.n_nodes, tot[1] / I.n_nodes, tot[2] / I.n_nodes};
+        const double c[3] = {tot[0] / I.n_nodes, tot[1] / I.n_nodes, tot[2] / I.n_nodes};
         const double *S = tot + 3;
         o[0] = c[0];
         o[1] = c[1];
@@ -1486,26 +1513,6 @@ __global__ void __launch_bounds__(256) reduce_inst_kernel(DevBatch b, const real
         o[9] = tot[9];
         o[10] = tot[10];
         o[11] = tot[11];
-    }
-}
-
-// Block per box: h^3 * sum of the values added by the last spread, from the
-// per-tile FP64 partials, in tile order.
-static __global__ void __launch_bounds__(256) reduce_box_kernel(DevGrid g, const double *__restrict__ red_tile,
-                                                         double *__restrict__ red_box)
-{
-    __shared__ double sh[256];
-    const BoxDev B = g.boxes[blockIdx.x];
-    const long long nt = (long long)B.T * B.T * B.T;
-    for (int d = 0; d < 3; ++d) {
-        double s = 0.0;
-        for (long long t = threadIdx.x; t < nt; t += blockDim.x)
-            s += red_tile[3 * (B.tile_base + t) + d];
-        double r = block_sum<256>(s, sh);
-        if (threadIdx.x == 0) {
-            red_box[6LL * blockIdx.x + d] = r;
-            red_box[6LL * blockIdx.x + 3 + d] = 0.0;
-        }
     }
 }
 
