@@ -576,6 +576,107 @@ __global__ void bend_pass2_kernel(DevBatch b, const real *__restrict__ x, const 
     }
 }
 
+// ------------------------------------------------------- FP32 bending helpers
+// The same discrete operators as bend_vertex_pass1/2 (Meyer et al. 2003),
+// arranged for FP32 throughput. Per incident triangle (k, j, l) with
+// e1 = x_j - x_k, e2 = x_l - x_k: 2A = |e1 x e2| from one rsqrt, the corner
+// dots d_k = e1.e2, d_j = |e1|^2 - d_k, d_l = |e2|^2 - d_k, cotangents d/2A.
+// The corner-angle sum enters only through 2 pi - sum(theta); it is taken as
+// -arg(prod_t (cos theta_t + i sin theta_t)), one atan2 per vertex, which
+// equals the deficit while it lies in (-pi, pi) (any vertex of a closed mesh
+// that is not folded onto itself).
+struct RingF {
+    float e1[3], e2[3], fn[3], inv2A, dk, dj, dl, l1, l2;
+};
+__device__ __forceinline__ void ring_tri_f32(const float xk[3], const float xj[3], const float xl[3], RingF &t)
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        t.e1[a] = xj[a] - xk[a];
+        t.e2[a] = xl[a] - xk[a];
+    }
+    t.fn[0] = t.e1[1] * t.e2[2] - t.e1[2] * t.e2[1];
+    t.fn[1] = t.e1[2] * t.e2[0] - t.e1[0] * t.e2[2];
+    t.fn[2] = t.e1[0] * t.e2[1] - t.e1[1] * t.e2[0];
+    t.inv2A = rsqrtf(t.fn[0] * t.fn[0] + t.fn[1] * t.fn[1] + t.fn[2] * t.fn[2]);
+    t.l1 = t.e1[0] * t.e1[0] + t.e1[1] * t.e1[1] + t.e1[2] * t.e1[2];
+    t.l2 = t.e2[0] * t.e2[0] + t.e2[1] * t.e2[1] + t.e2[2] * t.e2[2];
+    t.dk = t.e1[0] * t.e2[0] + t.e1[1] * t.e2[1] + t.e1[2] * t.e2[2];
+    t.dj = t.l1 - t.dk;
+    t.dl = t.l2 - t.dk;
+}
+
+// Pass 1 at vertex k (positions in shared memory, SoA with stride nn):
+// mixed area A, kH = (K.n)/2 with K the cotangent mean-curvature vector over
+// 2A, kG = deficit / A, unit normal n (area-weighted face normals).
+__device__ __forceinline__ void bend1_f32(const TmplDev &T, int k, const float *xs, int nn, float &A_out,
+                                          float &kH_out, float &kG_out, float n_out[3])
+{
+    float K[3] = {0.f, 0.f, 0.f}, nrm[3] = {0.f, 0.f, 0.f}, A = 0.f, zr = 1.f, zi = 0.f;
+    const float xk[3] = {xs[k], xs[nn + k], xs[2 * nn + k]};
+    for (int q = T.inc_off[k]; q < T.inc_off[k + 1]; ++q) {
+        const int2 jl = T.ring[q];
+        const float xj[3] = {xs[jl.x], xs[nn + jl.x], xs[2 * nn + jl.x]};
+        const float xl[3] = {xs[jl.y], xs[nn + jl.y], xs[2 * nn + jl.y]};
+        RingF t;
+        ring_tri_f32(xk, xj, xl, t);
+        const float cj = t.dj * t.inv2A, cl = t.dl * t.inv2A;
+        // K += cot_l (x_k - x_j) + cot_j (x_k - x_l)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            K[a] -= cl * t.e1[a] + cj * t.e2[a];
+        const float twoA = (t.fn[0] * t.fn[0] + t.fn[1] * t.fn[1] + t.fn[2] * t.fn[2]) * t.inv2A;
+        float Ai;
+        if (t.dk >= 0.f && t.dj >= 0.f && t.dl >= 0.f)
+            Ai = (cl * t.l1 + cj * t.l2) * 0.125f;
+        else
+            Ai = t.dk < 0.f ? twoA * 0.25f : twoA * 0.125f;
+        A += Ai;
+        // unit (cos, sin) of the corner angle at k, |e1||e2| = sqrt(l1 l2)
+        const float r = rsqrtf(t.l1 * t.l2);
+        const float cr = t.dk * r, ci = twoA * r;
+        const float nr = zr * cr - zi * ci;
+        zi = zr * ci + zi * cr;
+        zr = nr;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            nrm[a] += t.fn[a];
+    }
+    const float rn = rsqrtf(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+    const float h = 0.5f / A;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        n_out[a] = nrm[a] * rn;
+        K[a] *= h;
+    }
+    A_out = A;
+    kH_out = 0.5f * (K[0] * n_out[0] + K[1] * n_out[1] + K[2] * n_out[2]);
+    kG_out = -atan2f(zi, zr) / A;
+}
+
+// Pass 2 at vertex k: lap = sum (cot_l (kH_j - kH_k) + cot_j (kH_l - kH_k))
+// and the unnormalised normal, in the order of pass 1.
+__device__ __forceinline__ void bend2_f32(const TmplDev &T, int k, const float *xs, const float *kHs, int nn,
+                                          float &lap_out, float nrm[3])
+{
+    float lap = 0.f;
+    nrm[0] = nrm[1] = nrm[2] = 0.f;
+    const float xk[3] = {xs[k], xs[nn + k], xs[2 * nn + k]};
+    const float kHk = kHs[k];
+    for (int q = T.inc_off[k]; q < T.inc_off[k + 1]; ++q) {
+        const int2 jl = T.ring[q];
+        const float xj[3] = {xs[jl.x], xs[nn + jl.x], xs[2 * nn + jl.x]};
+        const float xl[3] = {xs[jl.y], xs[nn + jl.y], xs[2 * nn + jl.y]};
+        RingF t;
+        ring_tri_f32(xk, xj, xl, t);
+        lap += (t.dl * t.inv2A) * (kHs[jl.x] - kHk) + (t.dj * t.inv2A) * (kHs[jl.y] - kHk);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            nrm[a] += t.fn[a];
+    }
+    lap_out = lap;
+}
+
 // ------------------------------------------------------------ FP32 fused path
 // One CTA per instance: node positions and force accumulators in shared
 // memory, element forces added with shared-memory atomics (order not
@@ -648,14 +749,9 @@ static __global__ void __launch_bounds__(512, 2) forces_fused_f32_kernel(DevBatc
     }
     if (T.kind == 0 && T.kb != 0.0) {
         const float kb = (float)T.kb, kH0 = -0.5f * (float)T.c0;
-        auto ld = [&](int v, float p[3]) {
-            p[0] = xs[v];
-            p[1] = xs[nn + v];
-            p[2] = xs[2 * nn + v];
-        };
         for (int k = threadIdx.x; k < nn; k += blockDim.x) {
             float A, kH, kG, n[3];
-            bend_vertex_pass1<float>(T, k, ld, A, kH, kG, n);
+            bend1_f32(T, k, xs, nn, A, kH, kG, n);
             kHs[k] = kH;
             const float dh = kH - kH0;
             const float mag = 2.f * kb * (2.f * dh * (kH * kH - kG + kH0 * kH)) * A;
@@ -665,21 +761,8 @@ static __global__ void __launch_bounds__(512, 2) forces_fused_f32_kernel(DevBatc
         }
         __syncthreads();
         for (int k = threadIdx.x; k < nn; k += blockDim.x) {
-            float lap = 0.f, nrm[3] = {0.f, 0.f, 0.f};
-            const float kHk = kHs[k];
-            for (int q = T.inc_off[k]; q < T.inc_off[k + 1]; ++q) {
-                const int2 jk = T.ring[q];
-                float p[3][3];
-                ld(k, p[0]);
-                ld(jk.x, p[1]);
-                ld(jk.y, p[2]);
-                TriGeom<float> t;
-                tri_geom(p, t);
-                lap += (t.dot[2] / t.twoA) * (kHs[jk.x] - kHk) + (t.dot[1] / t.twoA) * (kHs[jk.y] - kHk);
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-                    nrm[a] += t.fn[a];
-            }
+            float lap, nrm[3];
+            bend2_f32(T, k, xs, kHs, nn, lap, nrm);
             const float s = kb * lap * rsqrtf(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
 #pragma unroll
             for (int a = 0; a < 3; ++a)
