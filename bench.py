@@ -38,11 +38,12 @@ WORKLOADS = {
            "each (capsules 642/2562, RBC 2562, Kuhn balls 512-3375 nodes), one launch per stage, 4-point delta"),
 }
 WORKLOAD = WORKLOADS["C4"]
+REF_BUDGET_S = 150.0   # --impl reference: warm-up + timed oracle steps
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of the current kernels on this workload (profiles/*_c4_fp32.md);
-# set an entry to None when its kernel changes.
+# ncu capture of the current kernels on the C4 suspension (profiles/*_c4_fp32.md),
+# reported for that workload only; set an entry to None when its kernel changes.
 NCU_TRAFFIC = {"spread+interp": 463.2e6, "spread": None, "interp": None, "forces": None, "bin": None}
 
 
@@ -140,20 +141,51 @@ def job_throughput(n_nodes_per_rank, world, t_ms):
     return world * n_nodes_per_rank / (t_ms * 1e-3)
 
 
+def _even_sample(wl, n_target):
+    """Evenly spaced particles whose node count first reaches n_target (at least one)."""
+    sizes = [wl.templates[i.tmpl].n_nodes for i in wl.instances]
+    if n_target >= sum(sizes):
+        return list(range(len(sizes))), int(sum(sizes))
+    k = 1
+    while True:
+        sel = sorted(set(np.linspace(0, len(sizes) - 1, k).astype(int).tolist()))
+        n = int(sum(sizes[i] for i in sel))
+        if n >= n_target or k >= len(sizes):
+            return sel, n
+        k += 1
+
+
+def _oracle_cost(wl, xl):
+    """Oracle step time as a + b * nodes (a: the grid work of a step), from two small samples."""
+    from oracle import oracle as O
+    pts = []
+    for n_target in (3000, 40000):
+        sel, n = _even_sample(wl, n_target)
+        t0 = time.perf_counter()
+        O.oracle_step(wl, x_local=xl, instances=sel)
+        pts.append((n, time.perf_counter() - t0))
+    (n1, t1), (n2, t2) = pts
+    b = max((t2 - t1) / max(n2 - n1, 1), 1e-9)
+    return max(t1 - b * n1, 0.0), b
+
+
 def run_reference(args, rank, world):
-    """The FP64 CPU oracle on the same workload (rank 0 only)."""
+    """The FP64 CPU oracle on the same workload (rank 0 only).
+
+    Each step is one oracle coupling step (forces, spread, interpolation, sums)
+    over a sample of the particles sized so that the warm-up and timed steps
+    together take about REF_BUDGET_S seconds; the whole suspension when that fits."""
     if rank != 0:
         return
     import ifem_workloads as W
     from oracle import oracle as O
     O.build()
-    wl = W.make("C4")
+    wl = W.make(args.workload)
     xl = wl.x_local_all(np.float32).astype(np.float64)
     N = wl.n_nodes
-    # bounded sample: every `stride`-th particle, sized to a few seconds per step
-    stride = 4
-    sel = list(range(0, len(wl.instances), stride))
-    n_sel = int(sum(wl.templates[wl.instances[i].tmpl].n_nodes for i in sel))
+    a, b = _oracle_cost(wl, xl)
+    per_step = REF_BUDGET_S / max(1, args.steps + max(0, args.warmup))
+    sel, n_sel = _even_sample(wl, int(max(0.0, per_step - a) / b))
     for _ in range(max(0, args.warmup)):
         O.oracle_step(wl, x_local=xl, instances=sel)
     ts = []
@@ -163,34 +195,37 @@ def run_reference(args, rank, world):
         ts.append(time.perf_counter() - t0)
     t = float(np.mean(ts))
     val = n_sel / t
+    sample = (f"{len(sel)} of {len(wl.instances)} particles evenly spaced ({n_sel} of {N} nodes), one full "
+              f"oracle step (forces + spread + interp + sums) on the whole grid per timed step, single thread")
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "nodes/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nodes": N, "grid": 256, "sample_nodes": n_sel},
-        "cpu_baseline": {"value": val, "unit": "nodes/s", "cores": 1, "kind": "oracle",
-                         "sample": f"every {stride}th particle of the suspension ({n_sel} nodes), one full "
-                                   "step (forces + spread + interp + sums) per timed step, single thread"},
+        "config": {"workload": WORKLOADS[args.workload], "nodes": N,
+                   "grid": [bx.n for bx in wl.boxes] if len(wl.boxes) > 1 else wl.boxes[0].n,
+                   "sample_nodes": n_sel},
+        "cpu_baseline": {"value": val, "unit": "nodes/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "nodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def cpu_baseline_sample(wl):
-    """Oracle timed on a bounded sample of the workload (host cores, one thread)."""
+    """Oracle timed on the whole workload (host cores, one thread): full coupling
+    steps repeated until at least 10 s of CPU work (at most 8 steps)."""
     from oracle import oracle as O
     O.build()
     xl = wl.x_local_all(np.float32).astype(np.float64)
-    stride = 4
-    sel = list(range(0, len(wl.instances), stride))
-    n_sel = int(sum(wl.templates[wl.instances[i].tmpl].n_nodes for i in sel))
-    O.oracle_step(wl, x_local=xl, instances=sel[:2])
-    t0 = time.perf_counter()
-    O.oracle_step(wl, x_local=xl, instances=sel)
-    t = time.perf_counter() - t0
-    return {"value": n_sel / t, "unit": "nodes/s", "cores": 1, "kind": "oracle",
-            "sample": f"every 4th particle ({n_sel} nodes), one full step (forces + spread + interp + "
-                      f"sums), single thread, {t:.1f} s"}
+    sel = list(range(len(wl.instances)))
+    ts = []
+    while sum(ts) < 10.0 and len(ts) < 8:
+        t0 = time.perf_counter()
+        O.oracle_step(wl, x_local=xl, instances=sel)
+        ts.append(time.perf_counter() - t0)
+    t = float(np.mean(ts))
+    return {"value": wl.n_nodes / t, "unit": "nodes/s", "cores": 1, "kind": "oracle",
+            "sample": f"the whole workload ({wl.n_nodes} nodes), {len(ts)} full oracle steps (forces + spread + "
+                      f"interp + sums), single thread, {sum(ts):.1f} s"}
 
 
 def main():
@@ -381,7 +416,7 @@ def main():
         "stage_ms": stage_ms,
         "touched_values": T, "pairs": P,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": NCU_TRAFFIC.get(dom), "peak_kind": peak_kind,
+                     "frac": achieved / hbm, "traffic": NCU_TRAFFIC.get(dom) if args.workload == "C4" else None, "peak_kind": peak_kind,
                      "algorithmic_bytes": ab[dom]},
         "cpu_baseline": cpu,
         "e2e": {"value": job_throughput(N, world, e2e_ms), "unit": "nodes/s", "h2d_bytes_per_step": 12 * N,
