@@ -660,6 +660,7 @@ static int ws_ensure(ifem_ctx ctx, ifem_batch b, ifem_grid g, int tile)
     CK(alloc((void **)&w.own_off, sizeof(int) * (no + 1)));
     CK(alloc((void **)&w.own_cursor, sizeof(int) * (no + 1)));
     CK(alloc((void **)&w.own_nodes, sizeof(int) * (size_t)std::max<long long>(N, 1)));
+    CK(alloc((void **)&w.own_rec, sizeof(float4) * (size_t)std::max<long long>(N, 1)));
     CK(alloc((void **)&w.active, sizeof(int) * (nt + 1)));
     CK(alloc((void **)&w.counters, sizeof(int) * 8));
     CK(alloc((void **)&w.scan_blocks, sizeof(int) * 2 * (nb + 1)));

@@ -108,6 +108,8 @@ struct DevWork {
     int *own_off;
     int *own_cursor;
     int *own_nodes;     // N entries: nodes grouped by the tile (and sub-block) of their cell
+    float4 *own_rec;    // beside own_nodes (FP32 halo path): fractional cell coordinates x, y, z of
+                        // the node and, in w, its cell within the tile packed as 8-bit x | y << 8 | z << 16
     int *active;        // tiles with candidate pairs
     int *counters;      // [0] n_active, [2] work counter, [4] total pairs, [5] total own nodes
     int *scan_blocks;   // block partial sums for the tile scan

@@ -82,25 +82,27 @@ __device__ inline bool node_cell(const InstDev &I, const BoxDev &B, const real *
 // atomic (count pass: the count; fill pass: the slot range). Every lane of
 // the warp must call this (invalid lanes pass valid = false).
 template <bool FILL>
-__device__ __forceinline__ void agg_append(int *count, int *cursor, int *list, long long tile, bool valid,
+__device__ __forceinline__ int agg_append(int *count, int *cursor, int *list, long long tile, bool valid,
                                            int node)
 {
     const unsigned key = valid ? (unsigned)tile : 0xffffffffu;
     const unsigned grp = __match_any_sync(0xffffffffu, key);
     if (!valid)
-        return;
+        return -1;
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(grp) - 1;
     if (!FILL) {
         if (lane == leader)
             atomicAdd(&count[tile], __popc(grp));
-    } else {
-        int base = 0;
-        if (lane == leader)
-            base = atomicAdd(&cursor[tile], __popc(grp));
-        base = __shfl_sync(grp, base, leader);
-        list[base + __popc(grp & ((1u << lane) - 1u))] = node;
+        return -1;
     }
+    int base = 0;
+    if (lane == leader)
+        base = atomicAdd(&cursor[tile], __popc(grp));
+    base = __shfl_sync(grp, base, leader);
+    const int slot = base + __popc(grp & ((1u << lane) - 1u));
+    list[slot] = node;
+    return slot;
 }
 
 // FILL = false: count candidate / own pairs per tile; FILL = true: write them.
@@ -138,9 +140,28 @@ __global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restr
               sbz = (c[2] - tile_start(oz, B.t)) >> 2;
     const long long own = (B.tile_base + ((long long)oz * B.T + oy) * B.T + ox) * kOwnSub3
                           + (sbz * kOwnSub + sby) * kOwnSub + sbx;
-    agg_append<FILL>(w.own_count, w.own_cursor, w.own_nodes, own, ok, node);
-    if (!with_cand)
+    const int slot = agg_append<FILL>(w.own_count, w.own_cursor, w.own_nodes, own, ok, node);
+    if (!with_cand) {
+        // halo-scatter spread: the node's fractional cell coordinates and its
+        // cell within the tile, beside its own-list entry (same arithmetic as
+        // node_cell, so the cell matches the tile it was binned into)
+        if constexpr (FILL && std::is_same<real, float>::value) {
+            if (slot >= 0) {
+                float fr[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    int I0;
+                    const float t = LatCoord<float>::get(I, B, a, x[a * b.N + node], 0.f, I0);
+                    fr[a] = t - floorf(t);
+                }
+                const unsigned pk = (unsigned)(c[0] - tile_start(ox, B.t)) |
+                                    ((unsigned)(c[1] - tile_start(oy, B.t)) << 8) |
+                                    ((unsigned)(c[2] - tile_start(oz, B.t)) << 16);
+                w.own_rec[slot] = make_float4(fr[0], fr[1], fr[2], __uint_as_float(pk));
+            }
+        }
         return;
+    }
 #pragma unroll
     for (int slot = 0; slot < 8; ++slot) {
         const int ix = slot & 1, iy = (slot >> 1) & 1, iz = slot >> 2;
@@ -407,16 +428,19 @@ struct FixedPoint<long long> {
 // (the radicands of both branches of phi reduce to the same 1 + 4r - 4r^2,
 // which lies in [1, 2], so sqrt(t) = t * rsqrt(t) needs no special cases).
 // Used by the FP32 kernels; the FP64 kernels evaluate phi point by point.
-__device__ __forceinline__ int peskin_axis_fast(float s, float ph[4])
+__device__ __forceinline__ void peskin_frac(float r, float ph[4])
 {
-    const float fl = floorf(s);
-    const float r = s - fl;
     const float t = 1.f + 4.f * r - 4.f * r * r;   // in [1, 2] for r in [0, 1)
     const float q = t * rsqrtf(t);
     ph[0] = (3.f - 2.f * r - q) * 0.125f;
     ph[1] = (3.f - 2.f * r + q) * 0.125f;
     ph[2] = (1.f + 2.f * r + q) * 0.125f;
     ph[3] = (1.f + 2.f * r - q) * 0.125f;
+}
+__device__ __forceinline__ int peskin_axis_fast(float s, float ph[4])
+{
+    const float fl = floorf(s);
+    peskin_frac(s - fl, ph);
     return (int)fl - 1;
 }
 
@@ -737,7 +761,7 @@ __host__ __device__ inline int halo_ints(int E)
 // lattice) unit also gathers u at the 64 stencil points with the unscaled
 // weights it has just computed, v_d = sum phi u_d (Algorithm step 4).
 template <bool INTERP>
-__global__ void __launch_bounds__(256) spread_halo_kernel(DevBatch b, DevGrid g, DevWork w,
+__global__ void __launch_bounds__(256, 5) spread_halo_kernel(DevBatch b, DevGrid g, DevWork w,
                                                           const float *__restrict__ x,
                                                           const float *__restrict__ F, float *__restrict__ f,
                                                           int density, const float *__restrict__ u,
@@ -814,27 +838,32 @@ __global__ void __launch_bounds__(256) spread_halo_kernel(DevBatch b, DevGrid g,
         const float gsc = sd * s_scale;
         for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
             const int node = w.own_nodes[q];
-            const InstDev &I = b.inst[b.node_inst[node]];
+            const float4 rec = w.own_rec[q];   // written by the binning
             const float gq = F[d * N + node] * gsc;
+            const unsigned pk = __float_as_uint(rec.w);
+            const float fr[3] = {rec.x, rec.y, rec.z};
             float ph[3][4];
             int l0[3];
             bool inside = true;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                // the cell coordinate exactly as the binning computes it, so
-                // the node's cell lies in this tile
-                int I0;
-                const float t = LatCoord<float>::get(I, s_B, a, x[a * N + node], 0.f, I0);
-                const float ft = floorf(t);
-                const int i0 = peskin_axis_fast(t - (a == d ? 0.f : 0.5f), ph[a]);   // floor(s) - 1
-                const int st = a == 0 ? sx : (a == 1 ? sy : sz);
-                const int c = wrap_near(I0 + (int)ft, n) - st;                        // cell within the tile
-                // stencil start in the buffer: i0 - floor(t) is -2 or -1
-                l0[a] = c + (a == 0 ? kHaloX : kHaloYZ) + (i0 - (int)ft);
+                // lattice d sits at the cell coordinate, the other two half a
+                // cell lower: s = t - 1/2 has floor(t) - 1 and fraction r + 1/2
+                // below r = 1/2, so the stencil starts 2 (not 1) cells below
+                const int c = (int)((pk >> (8 * a)) & 255u);   // cell within the tile
+                int sh = -1;
+                float r = fr[a];
+                if (a != d) {
+                    const bool low = r < 0.5f;
+                    r = low ? r + 0.5f : r - 0.5f;
+                    sh = low ? -2 : -1;
+                }
+                peskin_frac(r, ph[a]);
+                l0[a] = c + (a == 0 ? kHaloX : kHaloYZ) + sh;
                 const int lim = (a == 0 ? bx : (a == 1 ? by : bz)) - 4;
                 inside = inside && (unsigned)l0[a] <= (unsigned)lim;
             }
-            if (!inside) {   // only for coordinates beyond the range of int cells
+            if (!inside) {   // a record inconsistent with this tile: never expected
                 status_add(w.status, ST_DOMAIN, 1);
                 continue;
             }
