@@ -41,6 +41,11 @@
  *                    Algorithm steps 2 and 4.
  *   ifo_volume       the polyhedron volume of Sec. "Conservation of Volume
  *                    for Membranes".
+ *   ifo_interp_cc    interpolation S of a cell-centred multi-component
+ *                    field (the conformation tensor C of the same section).
+ *   ifo_tet_fluid_forces  the Newtonian and polymer fluid-stress parts of
+ *                    Eq. FEM inside solids (P^{f,N}, P^{f,P} of Sec.
+ *                    "Governing Equations" / "Numerical Implementation").
  */
 #include <math.h>
 #include <stdint.h>
@@ -290,6 +295,61 @@ int ifo_interp(int kernel, int n, double L, int N, const double *x, const double
                         }
             }
             v[3 * k + d] = acc;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Interpolation S of a cell-centred field with ncomp components (the   */
+/* conformation tensor C_J of Sec. "Interpolation Scheme"): every       */
+/* component sits at ((i,j,k) + 1/2) h, so s = p n/L - 1/2 on all axes. */
+/* Same stencil and order as ifo_interp: acc = acc + w * c_J from 0,    */
+/* z-outer, x-inner, w = (phi_x * phi_y) * phi_z (Peskin).              */
+/* field: ncomp blocks of n^3 values; out: (N, ncomp).                  */
+/* ------------------------------------------------------------------ */
+int ifo_interp_cc(int kernel, int n, double L, int N, const double *x, const double *field, int ncomp,
+                  double *out, double support)
+{
+    const double inv_h = (double)n / L;
+    const long n3 = (long)n * n * n;
+    for (int k = 0; k < N; ++k) {
+        double s[3];
+        for (int a = 0; a < 3; ++a)
+            s[a] = lattice_coord(x[3 * k + a], inv_h, 0.5);
+        double px[4], py[4], pz[4], w27[27];
+        long i0[3] = {0, 0, 0};
+        int base[3] = {0, 0, 0};
+        if (kernel == 0) {
+            i0[0] = peskin_axis(s[0], px);
+            i0[1] = peskin_axis(s[1], py);
+            i0[2] = peskin_axis(s[2], pz);
+        } else if (ifo_mls_weights(s, support, base, w27) != 0) {
+            return -1;
+        }
+        for (int q = 0; q < ncomp; ++q) {
+            const double *cq = field + q * n3;
+            double acc = 0.0;
+            if (kernel == 0) {
+                for (int c = 0; c < 4; ++c)
+                    for (int b = 0; b < 4; ++b)
+                        for (int a = 0; a < 4; ++a) {
+                            double w = (px[a] * py[b]) * pz[c];
+                            long idx = ((long)wrap(i0[2] + c, n) * n + wrap(i0[1] + b, n)) * n
+                                       + wrap(i0[0] + a, n);
+                            acc = acc + w * cq[idx];
+                        }
+            } else {
+                int J = 0;
+                for (int c = 0; c < 3; ++c)
+                    for (int b = 0; b < 3; ++b)
+                        for (int a = 0; a < 3; ++a, ++J) {
+                            long idx = ((long)wrap(base[2] + c, n) * n + wrap(base[1] + b, n)) * n
+                                       + wrap(base[0] + a, n);
+                            acc = acc + w27[J] * cq[idx];
+                        }
+            }
+            out[(long)ncomp * k + q] = acc;
         }
     }
     return 0;
@@ -623,6 +683,77 @@ int ifo_tet_forces(double lam, double mu, int nn, int ne, const int *tet, const 
                 Fout[3 * t[k] + i] = Fout[3 * t[k] + i] + f[k][i];
     }
     return inverted;
+}
+
+/* Fluid-stress nodal forces inside a solid (Sec. "Governing Equations": */
+/* F^IB = -int (P^s - P^{f,N} - P^{f,P}) grad N_k, so the fluid parts     */
+/* enter with a plus sign). Per tet, on the reference configuration:     */
+/*   F = Ds Dm^-1, J = det F, Fi = F^-1 (tet_defgrad, inv3);              */
+/*   G = Du Dm^-1 = sum_k u_k (x) grad N_k (nodal velocities u);           */
+/*   Lv[i][j] = (G[i][0]*Fi[0][j] + G[i][1]*Fi[1][j]) + G[i][2]*Fi[2][j]   */
+/*             (velocity gradient du_i/dx_j);                              */
+/*   E[i][j] = Lv[i][j] + Lv[j][i];                                        */
+/*   PN[i][j] = (eta*J) * ((E[i][0]*Fi[j][0] + E[i][1]*Fi[j][1])           */
+/*              + E[i][2]*Fi[j][2])   (eta J (grad u + grad u^T) F^-T);    */
+/*   Cb[i][j] = (((c_0 + c_1) + c_2) + c_3) * 0.25, c_k = C_k[i][j] - d_ij */
+/*   (the printed sum of (C_k - I)/4 over the four nodes);                 */
+/*   PP[i][j] = (J*cp) * ((Cb[i][0]*Fi[j][0] + Cb[i][1]*Fi[j][1])          */
+/*              + Cb[i][2]*Fi[j][2]),  cp = (eta*(1 - beta))/lambda;        */
+/*   P = PN + PP;  f_k[i] = V0*((P[i][0]*M[k][0] + P[i][1]*M[k][1])         */
+/*              + P[i][2]*M[k][2]) (k = 1..3), f_0[i] = -((f_1 + f_2) + f_3). */
+/* C: (N, 6) per node in the order xx, yy, zz, xy, xz, yz, or NULL (no    */
+/* polymer term). Tets ascending, Fout[node] = Fout[node] + f, from 0.    */
+void ifo_tet_fluid_forces(double eta, double beta, double lambda, int nn, int ne, const int *tet,
+                          const double *Dminv, const double *V0, const double *x, const double *u,
+                          const double *C, double *Fout)
+{
+    memset(Fout, 0, sizeof(double) * 3 * (size_t)nn);
+    const double cp = (eta * (1.0 - beta)) / lambda;
+    static const int sym[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+    for (int e = 0; e < ne; ++e) {
+        const int *t = tet + 4 * e;
+        const double *Mi = Dminv + 9 * e;
+        double F[3][3], G[3][3], Fi[3][3], Lv[3][3], E[3][3], P[3][3];
+        tet_defgrad(x, t, Mi, F);
+        tet_defgrad(u, t, Mi, G);
+        const double J = det3(F);
+        inv3(F, J, Fi);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                Lv[i][j] = (G[i][0] * Fi[0][j] + G[i][1] * Fi[1][j]) + G[i][2] * Fi[2][j];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                E[i][j] = Lv[i][j] + Lv[j][i];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                P[i][j] = (eta * J) * ((E[i][0] * Fi[j][0] + E[i][1] * Fi[j][1]) + E[i][2] * Fi[j][2]);
+        if (C) {
+            double Cb[3][3];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    const double dij = i == j ? 1.0 : 0.0;
+                    double acc = C[6 * t[0] + sym[i][j]] - dij;
+                    for (int k = 1; k < 4; ++k)
+                        acc = acc + (C[6 * t[k] + sym[i][j]] - dij);
+                    Cb[i][j] = acc * 0.25;
+                }
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    P[i][j] = P[i][j]
+                              + (J * cp) * ((Cb[i][0] * Fi[j][0] + Cb[i][1] * Fi[j][1]) + Cb[i][2] * Fi[j][2]);
+        }
+        double f[4][3];
+        for (int k = 1; k <= 3; ++k)
+            for (int i = 0; i < 3; ++i) {
+                const double *g = Mi + 3 * (k - 1);
+                f[k][i] = V0[e] * ((P[i][0] * g[0] + P[i][1] * g[1]) + P[i][2] * g[2]);
+            }
+        for (int i = 0; i < 3; ++i)
+            f[0][i] = -((f[1][i] + f[2][i]) + f[3][i]);
+        for (int k = 0; k < 4; ++k)
+            for (int i = 0; i < 3; ++i)
+                Fout[3 * t[k] + i] = Fout[3 * t[k] + i] + f[k][i];
+    }
 }
 
 /* Strain energy density of the compressible neo-Hookean solid:

@@ -76,6 +76,9 @@ def lib():
             L.ifo_bending_energy.argtypes = [d, d, i, i, p, p]
             L.ifo_volume.restype = d
             L.ifo_volume.argtypes = [i, p, p]
+            L.ifo_interp_cc.restype = i
+            L.ifo_interp_cc.argtypes = [i, i, d, i, p, p, i, p, d]
+            L.ifo_tet_fluid_forces.argtypes = [d, d, d, i, i, p, p, p, p, p, p, p]
             _lib = L
     return _lib
 
@@ -134,6 +137,19 @@ def interp(x_abs, u, n: int, L: float, kernel: int = KERNEL_PESKIN4,
     return v
 
 
+def interp_cc(x_abs, field, n: int, L: float, kernel: int = KERNEL_PESKIN4,
+              support: float = MLS_SUPPORT) -> np.ndarray:
+    """S of a cell-centred field (ncomp, n, n, n): returns (N, ncomp)."""
+    x_abs, field = _f64(x_abs), _f64(field)
+    ncomp = field.shape[0]
+    out = np.zeros((x_abs.shape[0], ncomp))
+    rc = lib().ifo_interp_cc(kernel, n, float(L), x_abs.shape[0], _ptr(x_abs), _ptr(field), ncomp, _ptr(out),
+                             support)
+    if rc != 0:
+        raise FloatingPointError("singular MLS moment matrix")
+    return out
+
+
 # ------------------------------------------------------------ membranes
 def membrane_reference(tri, X):
     tri, X = _i32(tri), _f64(X)
@@ -190,6 +206,17 @@ def tet_forces(lam, mu, tet, X, x, ref=None, return_inverted=False):
     inv = lib().ifo_tet_forces(lam, mu, x.shape[0], tet.shape[0], _ptr(tet), _ptr(Dminv), _ptr(V0),
                                _ptr(x), _ptr(F))
     return (F, inv) if return_inverted else F
+
+
+def tet_fluid_forces(eta, beta, lam_relax, tet, X, x, u, C=None, ref=None):
+    """Newtonian (+ polymer, if C (N, 6) is given) fluid-stress nodal forces of a solid."""
+    tet, x, u = _i32(tet), _f64(x), _f64(u)
+    Dminv, V0 = tet_reference(tet, X) if ref is None else ref
+    Cp = None if C is None else _f64(C)
+    F = np.zeros_like(x)
+    lib().ifo_tet_fluid_forces(eta, beta, lam_relax, x.shape[0], tet.shape[0], _ptr(tet), _ptr(Dminv), _ptr(V0),
+                               _ptr(x), _ptr(u), None if Cp is None else _ptr(Cp), _ptr(F))
+    return F
 
 
 def tet_energy(lam, mu, tet, X, x, ref=None) -> float:
