@@ -72,3 +72,25 @@ def sample_on_mac(modes, n: int, L: float, dtype=np.float64) -> np.ndarray:
             acc += (a * e[d] * np.exp(1j * f)) * (ez[:, None, None] * ey[None, :, None] * ex[None, None, :])
         out[d] = acc.real
     return out.astype(dtype, copy=False)
+
+
+def conformation_cc(rng: np.random.Generator, n: int, L: float, n_modes: int = 6, kmax: int = 3,
+                    amplitude: float = 0.05) -> np.ndarray:
+    """Seeded smooth cell-centred conformation-tensor field: (6, n, n, n) in the
+    component order xx, yy, zz, xy, xz, yz, equal to I plus a sum of cosine
+    modes with random symmetric amplitude matrices (the perturbation stays
+    below the identity, so every sample is symmetric positive definite)."""
+    c = (np.arange(n, dtype=np.float64) + 0.5) * (L / n)
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    out = np.zeros((6, n, n, n))
+    out[0] = out[1] = out[2] = 1.0
+    pairs = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))
+    for _ in range(n_modes):
+        k = rng.integers(-kmax, kmax + 1, size=3).astype(np.float64)
+        M = rng.standard_normal((3, 3))
+        M = amplitude * (M + M.T) / 2.0
+        arg = 2.0 * np.pi * (k[0] * X + k[1] * Y + k[2] * Z) / L + rng.uniform(0.0, 2.0 * np.pi)
+        cos = np.cos(arg)
+        for q, (i, j) in enumerate(pairs):
+            out[q] += M[i, j] * cos
+    return out

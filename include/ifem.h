@@ -262,6 +262,46 @@ int ifem_spread(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const vo
 int ifem_interpolate(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *u, const void *x,
                      void *v, void *stream);
 
+/* Interpolation S (Sec. "Interpolation Scheme") of a cell-centred field with
+ * ncomp components, e.g. the six components of the polymer conformation
+ * tensor C_J that the fluid-stress forces of solids need:
+ *   out_k,q = sum_J phi(x_J - (origin_k + x_k)) field_J,q,  x_J = ((i,j,k) + 1/2) h_b.
+ * field: device array, box b holding ncomp blocks of n_b^3 values (x fastest)
+ * from value offset (ifem_grid_box_offset(g, b) / 3) * ncomp; x: device node
+ * array; out: device array of ncomp rows of N (row q = component q), overwritten.
+ * ncomp in 1..64. Kernel and precision as the context; IFEM_FP64 order per
+ * node and component: acc = acc + w*c from 0, stencil z-outer, x-inner. */
+int ifem_interpolate_cc(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *field, int ncomp,
+                        const void *x, void *out, void *stream);
+
+/* Fluid properties for the fluid-stress forces inside solids: solvent +
+ * polymer viscosity eta, viscosity ratio beta, polymer relaxation time lambda
+ * (Sec. "Governing Equations"). */
+typedef struct {
+    double eta;
+    double beta;
+    double lambda;
+} ifem_fluid_params;
+
+/* ifem_fluid_stress_forces flags */
+#define IFEM_FORCES_ACCUMULATE 1 /* F = F + fluid forces (default: F overwritten) */
+
+/* Fluid-stress parts of the immersed-boundary force inside solid particles
+ * (Sec. "Governing Equations" and Eq. FEM with P^s - P^{f,N} - P^{f,P}):
+ *   F^N_k + F^P_k = V0 (P^{f,N} + P^{f,P}) grad N_k per tet, summed over tets,
+ *   P^{f,N} = eta J (grad u + grad u^T) F^-T,  grad u = sum_k u_k (x) grad N_k F^-1,
+ *   P^{f,P} = J eta (1 - beta)/lambda (sum_k (C_k - I)/4) F^-T.
+ * x: device node array (local positions); u: device node array of node
+ * velocities (e.g. from ifem_interpolate); C: device array of 6 rows of N
+ * (xx, yy, zz, xy, xz, yz, e.g. from ifem_interpolate_cc) or NULL for no
+ * polymer term; F: device node array, overwritten (or accumulated into with
+ * IFEM_FORCES_ACCUMULATE). Membrane nodes receive 0 (no fluid stress in the
+ * thin-shell model). Deterministic in both precisions (per-element buffer,
+ * then a fixed-order nodal sum); IFEM_FP64 follows the evaluation order
+ * written beside the kernel. IFEM_ERR_ARG for eta < 0 or, with C, lambda <= 0. */
+int ifem_fluid_stress_forces(ifem_ctx ctx, ifem_batch b, const void *x, const void *u, const void *C,
+                             const ifem_fluid_params *p, void *F, int flags, void *stream);
+
 /* FP64 conservation sums per instance i (ifem_reduce layout, 12 doubles):
  *   [0..2]  centroid c_i = mean of the local positions x_k
  *   [3..5]  sum_k F_k

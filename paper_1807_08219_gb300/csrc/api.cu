@@ -848,6 +848,51 @@ extern "C" int ifem_spread(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *
     return do_spread(ctx, b, g, x, F, f, flags, stream);
 }
 
+extern "C" int ifem_interpolate_cc(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *field, int ncomp,
+                                   const void *x, void *out, void *stream)
+{
+    int rc = check_call(ctx, b, g);
+    if (rc != IFEM_OK)
+        return rc;
+    if (!g || !field || ((!x || !out) && b->N > 0))
+        return fail(ctx, IFEM_ERR_ARG, "interpolate_cc: null array or grid");
+    if (ncomp < 1 || ncomp > 64)
+        return fail(ctx, IFEM_ERR_ARG, "interpolate_cc: ncomp must be 1..64");
+    if ((rc = ws_ensure(ctx, b, g, ctx->tile)) != IFEM_OK)
+        return rc;
+    TransferArgs a = transfer_args(ctx, b, x, nullptr, field, nullptr, out, 0, stream);
+    cudaError_t e = ctx->cfg.precision == IFEM_FP64 ? launch_interp_cc_f64(a, ncomp) : launch_interp_cc_f32(a, ncomp);
+    return launch_rc(ctx, e, "interpolate_cc");
+}
+
+extern "C" int ifem_fluid_stress_forces(ifem_ctx ctx, ifem_batch b, const void *x, const void *u, const void *C,
+                                        const ifem_fluid_params *p, void *F, int flags, void *stream)
+{
+    int rc = check_call(ctx, b, nullptr);
+    if (rc != IFEM_OK)
+        return rc;
+    if (!p || ((!x || !u || !F) && b->N > 0))
+        return fail(ctx, IFEM_ERR_ARG, "fluid_stress_forces: null array or parameters");
+    if (flags & ~IFEM_FORCES_ACCUMULATE)
+        return fail(ctx, IFEM_ERR_ARG, "fluid_stress_forces: unknown flags");
+    if (!(p->eta >= 0.0) || (C && !(p->lambda > 0.0)))
+        return fail(ctx, IFEM_ERR_ARG, "fluid_stress_forces: need eta >= 0 and, with C, lambda > 0");
+    FluidArgs a{};
+    a.b = dev_batch(b);
+    a.w.elem_buf = b->d_elem_buf;
+    a.w.status = ctx->d_status;
+    a.x = x;
+    a.u = u;
+    a.C = C;
+    a.eta = p->eta;
+    a.cp = C ? (p->eta * (1.0 - p->beta)) / p->lambda : 0.0;
+    a.add = (flags & IFEM_FORCES_ACCUMULATE) ? 1 : 0;
+    a.F = F;
+    a.stream = (cudaStream_t)stream;
+    cudaError_t e = ctx->cfg.precision == IFEM_FP64 ? launch_fluid_f64(a) : launch_fluid_f32(a);
+    return launch_rc(ctx, e, "fluid_stress_forces");
+}
+
 extern "C" int ifem_interpolate(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *u, const void *x, void *v,
                                 void *stream)
 {

@@ -343,4 +343,23 @@ cudaError_t launch_interp_f64(const TransferArgs &a);
 cudaError_t launch_reduce_f32(const ReduceArgs &a);
 cudaError_t launch_reduce_f64(const ReduceArgs &a);
 
+// Fluid-stress forces inside solids: F = (F +) sum of element contributions.
+struct FluidArgs {
+    DevBatch b;
+    DevWork w;
+    const void *x;
+    const void *u;
+    const void *C;    // 6 rows of N, or null
+    double eta;
+    double cp;        // eta (1 - beta) / lambda
+    int add;          // 1: F = F + fluid forces
+    void *F;
+    cudaStream_t stream;
+};
+cudaError_t launch_fluid_f32(const FluidArgs &a);
+cudaError_t launch_fluid_f64(const FluidArgs &a);
+// Cell-centred multi-component interpolation (TransferArgs.u = field).
+cudaError_t launch_interp_cc_f32(const TransferArgs &a, int ncomp);
+cudaError_t launch_interp_cc_f64(const TransferArgs &a, int ncomp);
+
 }  // namespace ifem

@@ -386,8 +386,8 @@ __global__ void elem_force_kernel(DevBatch b, const real *__restrict__ x, const 
 }
 
 // Thread per (instance, node): F = sum over incident (element, vertex) in
-// ascending element order, starting from 0: acc = acc + f.
-template <typename real>
+// ascending element order, starting from 0: acc = acc + f (ADD: F = F + acc).
+template <typename real, bool ADD = false>
 __global__ void node_gather_kernel(DevBatch b, const real *__restrict__ ebuf, real *__restrict__ F)
 {
     const int i = blockIdx.y;
@@ -406,8 +406,123 @@ __global__ void node_gather_kernel(DevBatch b, const real *__restrict__ ebuf, re
     }
     const long long N = b.N;
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-        F[a * N + I.node_off + k] = acc[a];
+    for (int a = 0; a < 3; ++a) {
+        real *p = F + a * N + I.node_off + k;
+        *p = ADD ? *p + acc[a] : acc[a];
+    }
+}
+
+// ------------------------------------------------------------ fluid stress
+// Newtonian and polymer fluid-stress parts of Eq. FEM inside a solid (Sec.
+// "Governing Equations"; they enter F^IB with a plus sign), per tet on the
+// reference configuration, in this order:
+//   F = Ds M, J = det F, Fi = F^-1; G = Du M = sum_k u_k (x) grad N_k;
+//   Lv[i][j] = (G[i][0] Fi[0][j] + G[i][1] Fi[1][j]) + G[i][2] Fi[2][j];
+//   E[i][j] = Lv[i][j] + Lv[j][i];
+//   P[i][j] = (eta J) ((E[i][0] Fi[j][0] + E[i][1] Fi[j][1]) + E[i][2] Fi[j][2]);
+//   polymer: Cb[i][j] = (((c_0 + c_1) + c_2) + c_3) * 0.25, c_k = C_k[i][j] - d_ij,
+//   P[i][j] = P[i][j] + (J cp) ((Cb[i][0] Fi[j][0] + Cb[i][1] Fi[j][1]) + Cb[i][2] Fi[j][2]),
+//   cp = eta (1 - beta) / lambda;
+//   f_k[i] = V0 ((P[i][0] M[k-1][0] + P[i][1] M[k-1][1]) + P[i][2] M[k-1][2]), k = 1..3;
+//   f_0[i] = -((f_1[i] + f_2[i]) + f_3[i]).
+// C per node: (xx, yy, zz, xy, xz, yz).
+template <typename real>
+__device__ __forceinline__ void tet_fluid_force(real eta, real cp, const real *M, real V0, const real x[4][3],
+                                                const real u[4][3], const real C[4][6], bool polymer,
+                                                real f[4][3])
+{
+    real F[3][3], G[3][3], Fi[3][3], Lv[3][3], E[3][3], P[3][3];
+    tet_F(x, M, F);
+    tet_F(u, M, G);
+    const real J = det3(F);
+    inv3(F, J, Fi);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            Lv[i][j] = (G[i][0] * Fi[0][j] + G[i][1] * Fi[1][j]) + G[i][2] * Fi[2][j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            E[i][j] = Lv[i][j] + Lv[j][i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            P[i][j] = (eta * J) * ((E[i][0] * Fi[j][0] + E[i][1] * Fi[j][1]) + E[i][2] * Fi[j][2]);
+    if (polymer) {
+        const int sym[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+        real Cb[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const real dij = i == j ? real(1) : real(0);
+                real acc = C[0][sym[i][j]] - dij;
+#pragma unroll
+                for (int k = 1; k < 4; ++k)
+                    acc = acc + (C[k][sym[i][j]] - dij);
+                Cb[i][j] = acc * real(0.25);
+            }
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                P[i][j] = P[i][j] + (J * cp) * ((Cb[i][0] * Fi[j][0] + Cb[i][1] * Fi[j][1]) + Cb[i][2] * Fi[j][2]);
+    }
+#pragma unroll
+    for (int k = 1; k <= 3; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const real *g = M + 3 * (k - 1);
+            f[k][i] = V0 * ((P[i][0] * g[0] + P[i][1] * g[1]) + P[i][2] * g[2]);
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        f[0][i] = -((f[1][i] + f[2][i]) + f[3][i]);
+}
+
+// Thread per (instance, element): the element's fluid-stress nodal forces
+// into elem_buf (zeros for membrane elements, which carry no fluid stress
+// in the paper's thin-shell model), then node_gather_kernel sums them.
+template <typename real>
+__global__ void fluid_elem_kernel(DevBatch b, const real *__restrict__ x, const real *__restrict__ u,
+                                  const real *__restrict__ C, real eta, real cp, real *__restrict__ ebuf)
+{
+    const InstDev I = b.inst[blockIdx.y];
+    const TmplDev T = b.tmpl[I.tmpl];
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= T.n_elems)
+        return;
+    real *out = ebuf + (I.elem_off + e) * 12;
+    if (T.kind == 0) {
+#pragma unroll
+        for (int i = 0; i < 12; ++i)
+            out[i] = real(0);
+        return;
+    }
+    const long long N = b.N;
+    real xs[4][3], us[4][3], Cs[4][6], f[4][3];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const long long v = I.node_off + T.elems[4 * e + c];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            xs[c][a] = x[a * N + v];
+            us[c][a] = u[a * N + v];
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+            Cs[c][q] = C ? C[q * N + v] : real(0);
+    }
+    const real *r = ref_ptr<real>(T) + 10 * e;
+    tet_fluid_force<real>(eta, cp, r, r[9], xs, us, Cs, C != nullptr, f);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            out[3 * c + a] = f[c][a];
 }
 
 // ------------------------------------------------------------ bending

@@ -10,4 +10,6 @@ cudaError_t launch_bin_f32(const TransferArgs &a, int det_sort, int with_cand)
 cudaError_t launch_spread_f32(const TransferArgs &a) { return spread_impl<float>(a); }
 cudaError_t launch_interp_f32(const TransferArgs &a) { return interp_impl<float>(a); }
 cudaError_t launch_reduce_f32(const ReduceArgs &a) { return reduce_impl<float>(a); }
+cudaError_t launch_fluid_f32(const FluidArgs &a) { return fluid_impl<float>(a); }
+cudaError_t launch_interp_cc_f32(const TransferArgs &a, int ncomp) { return interp_cc_impl<float>(a, ncomp); }
 }  // namespace ifem

@@ -13,4 +13,6 @@ cudaError_t launch_bin_f64(const TransferArgs &a, int det_sort, int with_cand)
 cudaError_t launch_spread_f64(const TransferArgs &a) { return spread_impl<double>(a); }
 cudaError_t launch_interp_f64(const TransferArgs &a) { return interp_impl<double>(a); }
 cudaError_t launch_reduce_f64(const ReduceArgs &a) { return reduce_impl<double>(a); }
+cudaError_t launch_fluid_f64(const FluidArgs &a) { return fluid_impl<double>(a); }
+cudaError_t launch_interp_cc_f64(const TransferArgs &a, int ncomp) { return interp_cc_impl<double>(a, ncomp); }
 }  // namespace ifem

@@ -174,4 +174,42 @@ cudaError_t reduce_impl(const ReduceArgs &a)
     return cudaSuccess;
 }
 
+template <typename real>
+cudaError_t fluid_impl(const FluidArgs &a)
+{
+    const DevBatch &b = a.b;
+    if (b.n_inst == 0)
+        return cudaSuccess;
+    dim3 blk(256);
+    dim3 ge((b.max_elems + 255) / 256, b.n_inst);
+    dim3 gn((b.max_nodes + 255) / 256, b.n_inst);
+    real *ebuf = (real *)a.w.elem_buf;
+    fluid_elem_kernel<real><<<ge, blk, 0, a.stream>>>(b, (const real *)a.x, (const real *)a.u, (const real *)a.C,
+                                                      (real)a.eta, (real)a.cp, ebuf);
+    IFEM_LAUNCH_CHECK();
+    if (a.add)
+        node_gather_kernel<real, true><<<gn, blk, 0, a.stream>>>(b, ebuf, (real *)a.F);
+    else
+        node_gather_kernel<real, false><<<gn, blk, 0, a.stream>>>(b, ebuf, (real *)a.F);
+    IFEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
+template <typename real>
+cudaError_t interp_cc_impl(const TransferArgs &a, int ncomp)
+{
+    const DevBatch &b = a.b;
+    if (b.n_inst == 0 || b.N == 0)
+        return cudaSuccess;
+    unsigned grid = (unsigned)((b.N + 255) / 256);
+    if (a.kernel == 0)
+        interp_cc_kernel<real, 0><<<grid, 256, 0, a.stream>>>(b, a.g, a.w, (const real *)a.u, ncomp,
+                                                              (const real *)a.x, (real *)a.v, (real)a.support);
+    else
+        interp_cc_kernel<real, 1><<<grid, 256, 0, a.stream>>>(b, a.g, a.w, (const real *)a.u, ncomp,
+                                                              (const real *)a.x, (real *)a.v, (real)a.support);
+    IFEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
 }  // namespace ifem

@@ -1388,6 +1388,106 @@ __global__ void __launch_bounds__(256) interp_kernel(DevBatch b, DevGrid g, DevW
     }
 }
 
+// ------------------------------------------- interpolation, cell-centred
+// S of a cell-centred field with ncomp components (the conformation tensor
+// C_J of Sec. "Interpolation Scheme"): all components at ((i,j,k) + 1/2) h.
+// Thread per node; the stencil weights are computed once and applied to
+// every component in the oracle's order: acc = acc + w * c_J from 0,
+// z-outer, x-inner, w = (phi_x * phi_y) * phi_z. Field layout: box b holds
+// ncomp blocks of n_b^3 values from (grid_off_b / 3) * ncomp; out: ncomp
+// rows of N.
+template <typename real, int KER>
+__global__ void __launch_bounds__(256) interp_cc_kernel(DevBatch b, DevGrid g, DevWork w,
+                                                        const real *__restrict__ field, int ncomp,
+                                                        const real *__restrict__ x, real *__restrict__ out,
+                                                        real support)
+{
+    const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (node >= b.N)
+        return;
+    const InstDev I = b.inst[b.node_inst[node]];
+    const BoxDev B = g.boxes[I.box];
+    const long long N = b.N;
+    const int n = B.n;
+    const long long n3 = (long long)n * n * n;
+    const real *fb = field + (B.grid_off / 3) * ncomp;
+    real xl[3];
+    bool finite = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        xl[a] = x[a * N + node];
+        finite = finite && isfinite(xl[a]);
+    }
+    if (!finite) {
+        status_add(w.status, ST_DOMAIN, 1);
+        for (int q = 0; q < ncomp; ++q)
+            out[q * N + node] = xl[0] + xl[1] + xl[2];
+        return;
+    }
+    if constexpr (KER == 0) {
+        real ph[3][4];
+        int ix[4], iy[4], iz[4];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int I0;
+            real s = LatCoord<real>::get(I, B, a, xl[a], real(0.5), I0);
+            long long i0 = peskin_axis<real>(s, ph[a]);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                int wi = wrapi(I0 + i0 + m, n);
+                if (a == 0) ix[m] = wi;
+                else if (a == 1) iy[m] = wi;
+                else iz[m] = wi;
+            }
+        }
+        for (int q = 0; q < ncomp; ++q) {
+            const real *cq = fb + q * n3;
+            real acc = real(0);
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb)
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        real wgt = (ph[0][a] * ph[1][bb]) * ph[2][c];
+                        acc = acc + wgt * cq[((long long)iz[c] * n + iy[bb]) * n + ix[a]];
+                    }
+            out[q * N + node] = acc;
+        }
+    } else {
+        real s[3];
+        int I0[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            s[a] = LatCoord<real>::get(I, B, a, xl[a], real(0.5), I0[a]);
+        int base[3];
+        real wt[27];
+        if (!mls_weights<real>(s, support, base, wt)) {
+            status_add(w.status, ST_DOMAIN, 1);
+            for (int q = 0; q < ncomp; ++q)
+                out[q * N + node] = real(0);
+            return;
+        }
+        for (int q = 0; q < ncomp; ++q) {
+            const real *cq = fb + q * n3;
+            real acc = real(0);
+            int J = 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a, ++J) {
+                        long long gi = ((long long)wrapi((long long)I0[2] + base[2] + c, n) * n
+                                        + wrapi((long long)I0[1] + base[1] + bb, n)) * n
+                                       + wrapi((long long)I0[0] + base[0] + a, n);
+                        acc = acc + wt[J] * cq[gi];
+                    }
+            out[q * N + node] = acc;
+        }
+    }
+}
+
 // ------------------------------------------------------------- reductions
 // Block per instance: FP64 sums in a fixed order (per-thread strided sums,
 // then a fixed shared-memory tree). Layout: 12 doubles per instance.

@@ -27,6 +27,7 @@ IFEM_KERNEL_PESKIN4, IFEM_KERNEL_MLS27 = 0, 1
 IFEM_SCATTER_DET, IFEM_SCATTER_ATOMIC = 0, 1
 IFEM_LAW_NEO_HOOKE, IFEM_LAW_SKALAK = 0, 1
 IFEM_SPREAD_DENSITY, IFEM_SPREAD_FORCE, IFEM_SPREAD_OVERWRITE = 0, 1, 2
+IFEM_FORCES_ACCUMULATE = 1
 
 # Every entry point declared in include/ifem.h.
 EXPORTS = (
@@ -36,6 +37,7 @@ EXPORTS = (
     "ifem_batch_create", "ifem_batch_destroy", "ifem_batch_nodes", "ifem_batch_instances",
     "ifem_batch_set_origins", "ifem_prepare", "ifem_compute_forces", "ifem_spread", "ifem_interpolate",
     "ifem_reduce", "ifem_step_coupling", "ifem_force_hvp", "ifem_compute_forces_noalloc",
+    "ifem_interpolate_cc", "ifem_fluid_stress_forces",
 )
 
 
@@ -52,6 +54,10 @@ class ifem_membrane_params(ctypes.Structure):
 
 class ifem_solid_params(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("mu", ctypes.c_double)]
+
+
+class ifem_fluid_params(ctypes.Structure):
+    _fields_ = [("eta", ctypes.c_double), ("beta", ctypes.c_double), ("lambda_", ctypes.c_double)]
 
 
 class ifem_instance_desc(ctypes.Structure):
@@ -115,6 +121,8 @@ def load(build_if_missing: bool = True):
         "ifem_step_coupling": (i, [p, p, p, p, p, p, p, p, p, i, p]),
         "ifem_force_hvp": (i, [p, p, p, p, p, p]),
         "ifem_compute_forces_noalloc": (i, [p, p, p, p, p]),
+        "ifem_interpolate_cc": (i, [p, p, p, p, i, p, p, p]),
+        "ifem_fluid_stress_forces": (i, [p, p, p, p, p, p, p, i, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -279,6 +287,18 @@ def ifem_spread(ctx, b, g, x, F, f, flags: int = 0, stream=None):
 
 def ifem_interpolate(ctx, b, g, u, x, v, stream=None):
     return _check(ctx, load().ifem_interpolate(ctx, b, g, _ptr(u), _ptr(x), _ptr(v), _stream(stream)))
+
+
+def ifem_interpolate_cc(ctx, b, g, field, ncomp: int, x, out, stream=None):
+    return _check(ctx, load().ifem_interpolate_cc(ctx, b, g, _ptr(field), int(ncomp), _ptr(x), _ptr(out),
+                                                  _stream(stream)))
+
+
+def ifem_fluid_stress_forces(ctx, b, x, u, C, eta: float, beta: float, lam: float, F, flags: int = 0,
+                             stream=None):
+    prm = ifem_fluid_params(eta, beta, lam)
+    return _check(ctx, load().ifem_fluid_stress_forces(ctx, b, _ptr(x), _ptr(u), _ptr(C), ctypes.byref(prm),
+                                                       _ptr(F), flags, _stream(stream)))
 
 
 def ifem_reduce(ctx, b, x, F, v, red, stream=None):
