@@ -46,6 +46,10 @@
  *   ifo_tet_fluid_forces  the Newtonian and polymer fluid-stress parts of
  *                    Eq. FEM inside solids (P^{f,N}, P^{f,P} of Sec.
  *                    "Governing Equations" / "Numerical Implementation").
+ *   ifo_ab2          the Adams-Bashforth position update (Eq. Bashforth_eqn).
+ *   ifo_tet_volume   the current volume of a solid (sum of tet volumes).
+ *   ifo_volume_correction  the membrane volume correction of Sec.
+ *                    "Conservation of Volume for Membranes".
  */
 #include <math.h>
 #include <stdint.h>
@@ -1003,4 +1007,105 @@ double ifo_volume(int nt, const int *tri, const double *x)
         V += dot3(a, t1) + dot3(b, t2) + dot3(c, t3);
     }
     return V / 18.0;
+}
+
+/* Volume of a solid in its current configuration: the sum of its tets'
+ * signed volumes det(Ds)/6, Ds = [x1-x0, x2-x0, x3-x0], tets ascending. */
+double ifo_tet_volume(int ne, const int *tet, const double *x)
+{
+    double V = 0.0;
+    for (int e = 0; e < ne; ++e) {
+        const int *t = tet + 4 * e;
+        double Ds[3][3];
+        for (int c = 0; c < 3; ++c)
+            for (int i = 0; i < 3; ++i)
+                Ds[i][c] = x[3 * t[1 + c] + i] - x[3 * t[0] + i];
+        V = V + det3(Ds) / 6.0;
+    }
+    return V;
+}
+
+/* Adams-Bashforth position update (Eq. Bashforth_eqn):
+ * x = x + dt*(1.5*v - 0.5*vp), componentwise, in place. */
+void ifo_ab2(int n3, double *x, const double *v, const double *vp, double dt)
+{
+    for (int i = 0; i < n3; ++i)
+        x[i] = x[i] + dt * (1.5 * v[i] - 0.5 * vp[i]);
+}
+
+/* Sum over faces (a, b, c) of the three cyclic triple products
+ * p_a.(q_b x r_c) + p_b.(q_c x r_a) + p_c.(q_a x r_b), faces ascending. */
+static double cyclic_triple_sum(int nt, const int *tri, const double *p, const double *q, const double *r)
+{
+    double s = 0.0;
+    for (int e = 0; e < nt; ++e) {
+        const int a = tri[3 * e], b = tri[3 * e + 1], c = tri[3 * e + 2];
+        double t1[3], t2[3], t3[3];
+        cross3(q + 3 * b, r + 3 * c, t1);
+        cross3(q + 3 * c, r + 3 * a, t2);
+        cross3(q + 3 * a, r + 3 * b, t3);
+        s += dot3(p + 3 * a, t1) + dot3(p + 3 * b, t2) + dot3(p + 3 * c, t3);
+    }
+    return s;
+}
+
+/* Volume conservation of a closed membrane (Sec. "Conservation of Volume
+ * for Membranes", after Mendez et al. 2014): the smallest displacement
+ * that restores the volume V0 is dx_I = Lambda alpha_I with
+ *   alpha_I = -(1/12) sum_{faces with I} x_{I2} x x_{I3} (the face's other
+ *   two nodes in cyclic order), accumulated over faces ascending, then
+ *   scaled by -1/12;
+ * Lambda the root of A L^3 + B L^2 + C L + D = 0 with the paper's
+ *   A = (1/18) sum [alpha . (alpha x alpha)] (cyclic),
+ *   B = (1/6)  sum [x . (alpha x alpha)] (cyclic),
+ *   C = (1/6)  sum [alpha . (x x x)] (cyclic),
+ *   D = V(x) - V0.
+ * The root taken is the one Newton's method reaches from Lambda = 0
+ * (the small correction): L = L - f/f', f = ((A L + B) L + C) L + D,
+ * f' = (3 A L + 2 B) L + C, until |step| <= 1e-15 max(1, |L|) (at most
+ * 100 steps). Then x_I = x_I + Lambda alpha_I. alpha: (nn, 3) scratch.
+ * Returns the Newton steps taken, or -1 if f' vanished or it did not converge. */
+int ifo_volume_correction(int nn, int nt, const int *tri, double *x, double V0, double *alpha,
+                          double *lambda_out)
+{
+    memset(alpha, 0, sizeof(double) * 3 * (size_t)nn);
+    for (int e = 0; e < nt; ++e) {
+        const int a = tri[3 * e], b = tri[3 * e + 1], c = tri[3 * e + 2];
+        double t[3];
+        cross3(x + 3 * b, x + 3 * c, t);
+        for (int i = 0; i < 3; ++i)
+            alpha[3 * a + i] = alpha[3 * a + i] + t[i];
+        cross3(x + 3 * c, x + 3 * a, t);
+        for (int i = 0; i < 3; ++i)
+            alpha[3 * b + i] = alpha[3 * b + i] + t[i];
+        cross3(x + 3 * a, x + 3 * b, t);
+        for (int i = 0; i < 3; ++i)
+            alpha[3 * c + i] = alpha[3 * c + i] + t[i];
+    }
+    for (int i = 0; i < 3 * nn; ++i)
+        alpha[i] = alpha[i] * (-1.0 / 12.0);
+    const double A = cyclic_triple_sum(nt, tri, alpha, alpha, alpha) / 18.0;
+    const double B = cyclic_triple_sum(nt, tri, x, alpha, alpha) / 6.0;
+    const double C = cyclic_triple_sum(nt, tri, alpha, x, x) / 6.0;
+    const double D = cyclic_triple_sum(nt, tri, x, x, x) / 18.0 - V0;
+    double L = 0.0;
+    int it = 0, ok = 0;
+    for (; it < 100; ++it) {
+        const double f = ((A * L + B) * L + C) * L + D;
+        const double fp = (3.0 * A * L + 2.0 * B) * L + C;
+        if (fp == 0.0)
+            break;
+        const double step = f / fp;
+        L = L - step;
+        if (fabs(step) <= 1e-15 * fmax(1.0, fabs(L))) {
+            ok = 1;
+            ++it;
+            break;
+        }
+    }
+    for (int i = 0; i < 3 * nn; ++i)
+        x[i] = x[i] + L * alpha[i];
+    if (lambda_out)
+        *lambda_out = L;
+    return ok ? it : -1;
 }

@@ -79,6 +79,11 @@ def lib():
             L.ifo_interp_cc.restype = i
             L.ifo_interp_cc.argtypes = [i, i, d, i, p, p, i, p, d]
             L.ifo_tet_fluid_forces.argtypes = [d, d, d, i, i, p, p, p, p, p, p, p]
+            L.ifo_tet_volume.restype = d
+            L.ifo_tet_volume.argtypes = [i, p, p]
+            L.ifo_ab2.argtypes = [i, p, p, p, d]
+            L.ifo_volume_correction.restype = i
+            L.ifo_volume_correction.argtypes = [i, i, p, p, d, p, p]
             _lib = L
     return _lib
 
@@ -260,6 +265,32 @@ def bending_energy(kb, tri, x, c0: float = 0.0) -> float:
 def volume(tri, x) -> float:
     tri, x = _i32(tri), _f64(x)
     return lib().ifo_volume(tri.shape[0], _ptr(tri), _ptr(x))
+
+
+def tet_volume(tet, x) -> float:
+    tet, x = _i32(tet), _f64(x)
+    return lib().ifo_tet_volume(tet.shape[0], _ptr(tet), _ptr(x))
+
+
+def ab2(x, v, vp, dt: float):
+    """Adams-Bashforth step: returns x + dt (3/2 v - 1/2 vp)."""
+    out = _f64(x).copy()
+    v, vp = _f64(v), _f64(vp)
+    lib().ifo_ab2(out.size, _ptr(out), _ptr(v), _ptr(vp), float(dt))
+    return out
+
+
+def volume_correction(tri, x, V0: float):
+    """Volume-corrected positions, the displacement directions alpha and Lambda."""
+    tri = _i32(tri)
+    out = _f64(x).copy()
+    alpha = np.zeros_like(out)
+    lam = ctypes.c_double(0.0)
+    it = lib().ifo_volume_correction(out.shape[0], tri.shape[0], _ptr(tri), _ptr(out), float(V0), _ptr(alpha),
+                                     ctypes.byref(lam))
+    if it < 0:
+        raise FloatingPointError("volume correction: Newton did not converge")
+    return out, alpha, lam.value
 
 
 # ------------------------------------------------------------ whole step
