@@ -302,6 +302,39 @@ typedef struct {
 int ifem_fluid_stress_forces(ifem_ctx ctx, ifem_batch b, const void *x, const void *u, const void *C,
                              const ifem_fluid_params *p, void *F, int flags, void *stream);
 
+/* ------------------------------------------------------ Lagrangian update */
+/* Adams-Bashforth position update (Eq. Bashforth_eqn), in place:
+ *   x = x + dt (3/2 v - 1/2 v_prev)
+ * x, v, v_prev: device node arrays (x: the particles' local positions).
+ * IFEM_FP64 evaluates x + dt*(1.5*v - 0.5*v_prev) in that order. For the
+ * first step pass v_prev = v (forward Euler). IFEM_ERR_ARG for a non-finite dt. */
+int ifem_ab2_update(ifem_ctx ctx, ifem_batch b, void *x, const void *v, const void *v_prev, double dt,
+                    void *stream);
+
+/* Current volume of every particle, FP64 in both precisions: membranes by the
+ * polyhedron formula of Sec. "Conservation of Volume for Membranes",
+ *   V = 1/18 sum_faces [x1.(x2 x x3) + x2.(x3 x x1) + x3.(x1 x x2)],
+ * solids as the sum of their tets' signed volumes det(Ds)/6. x: device node
+ * array; vol: device double array of n_inst, overwritten. Fixed-order block
+ * sums: reproducible run to run. */
+int ifem_volumes(ifem_ctx ctx, ifem_batch b, const void *x, double *vol, void *stream);
+
+/* Membrane volume correction (Sec. "Conservation of Volume for Membranes",
+ * after Mendez et al. 2014), in place: x_I = x_I + Lambda alpha_I with
+ *   alpha_I = -(1/12) sum over the faces containing I of x_I2 x x_I3 (the
+ *             face's other two nodes in cyclic order),
+ * Lambda the root, reached by Newton's method from 0, of
+ *   A L^3 + B L^2 + C L + D = 0, A = 1/18 sum alpha.(alpha x alpha),
+ *   B = 1/6 sum x.(alpha x alpha), C = 1/6 sum alpha.(x x x) (all cyclic over
+ *   each face's nodes), D = V(x) - V0.
+ * FP64 throughout (positions converted). V0: device double array of n_inst
+ * target volumes; lambda: device double array of n_inst receiving Lambda
+ * (0 for solids, which are left unchanged), or NULL. An instance whose Newton
+ * iteration does not converge in 100 steps is left unchanged and counted in
+ * domain_errors. Uses the batch's internal scratch: calls on one batch must
+ * not overlap on the GPU. */
+int ifem_volume_correct(ifem_ctx ctx, ifem_batch b, void *x, const double *V0, double *lambda, void *stream);
+
 /* FP64 conservation sums per instance i (ifem_reduce layout, 12 doubles):
  *   [0..2]  centroid c_i = mean of the local positions x_k
  *   [3..5]  sum_k F_k

@@ -848,6 +848,63 @@ extern "C" int ifem_spread(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *
     return do_spread(ctx, b, g, x, F, f, flags, stream);
 }
 
+static LagrangeArgs lagrange_args(ifem_ctx ctx, ifem_batch b, void *x, void *stream)
+{
+    LagrangeArgs a{};
+    a.b = dev_batch(b);
+    a.x = x;
+    a.status = ctx->d_status;
+    a.alpha = (double *)b->d_bend_buf;   // 6 reals per node: room for 3 doubles in either precision
+    a.stream = (cudaStream_t)stream;
+    return a;
+}
+
+extern "C" int ifem_ab2_update(ifem_ctx ctx, ifem_batch b, void *x, const void *v, const void *v_prev, double dt,
+                               void *stream)
+{
+    int rc = check_call(ctx, b, nullptr);
+    if (rc != IFEM_OK)
+        return rc;
+    if ((!x || !v || !v_prev) && b->N > 0)
+        return fail(ctx, IFEM_ERR_ARG, "ab2_update: null array");
+    if (!std::isfinite(dt))
+        return fail(ctx, IFEM_ERR_ARG, "ab2_update: dt must be finite");
+    LagrangeArgs a = lagrange_args(ctx, b, x, stream);
+    a.v = v;
+    a.vp = v_prev;
+    a.dt = dt;
+    cudaError_t e = ctx->cfg.precision == IFEM_FP64 ? launch_ab2_f64(a) : launch_ab2_f32(a);
+    return launch_rc(ctx, e, "ab2_update");
+}
+
+extern "C" int ifem_volumes(ifem_ctx ctx, ifem_batch b, const void *x, double *vol, void *stream)
+{
+    int rc = check_call(ctx, b, nullptr);
+    if (rc != IFEM_OK)
+        return rc;
+    if ((!x && b->N > 0) || (!vol && !b->inst.empty()))
+        return fail(ctx, IFEM_ERR_ARG, "volumes: null array");
+    LagrangeArgs a = lagrange_args(ctx, b, const_cast<void *>(x), stream);
+    a.out = vol;
+    cudaError_t e = ctx->cfg.precision == IFEM_FP64 ? launch_volume_f64(a) : launch_volume_f32(a);
+    return launch_rc(ctx, e, "volumes");
+}
+
+extern "C" int ifem_volume_correct(ifem_ctx ctx, ifem_batch b, void *x, const double *V0, double *lambda,
+                                   void *stream)
+{
+    int rc = check_call(ctx, b, nullptr);
+    if (rc != IFEM_OK)
+        return rc;
+    if ((!x && b->N > 0) || (!V0 && !b->inst.empty()))
+        return fail(ctx, IFEM_ERR_ARG, "volume_correct: null array");
+    LagrangeArgs a = lagrange_args(ctx, b, x, stream);
+    a.V0 = V0;
+    a.out = lambda;
+    cudaError_t e = ctx->cfg.precision == IFEM_FP64 ? launch_vcorr_f64(a) : launch_vcorr_f32(a);
+    return launch_rc(ctx, e, "volume_correct");
+}
+
 extern "C" int ifem_interpolate_cc(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *field, int ncomp,
                                    const void *x, void *out, void *stream)
 {

@@ -362,4 +362,24 @@ cudaError_t launch_fluid_f64(const FluidArgs &a);
 cudaError_t launch_interp_cc_f32(const TransferArgs &a, int ncomp);
 cudaError_t launch_interp_cc_f64(const TransferArgs &a, int ncomp);
 
+// Lagrangian update: AB2 positions, volumes, membrane volume correction.
+struct LagrangeArgs {
+    DevBatch b;
+    void *x;
+    const void *v;
+    const void *vp;
+    double dt;
+    const double *V0;
+    double *out;      // volumes, or Lambda per instance (may be null for the correction)
+    double *alpha;    // 3 doubles per node of scratch (correction)
+    unsigned long long *status;
+    cudaStream_t stream;
+};
+cudaError_t launch_ab2_f32(const LagrangeArgs &a);
+cudaError_t launch_ab2_f64(const LagrangeArgs &a);
+cudaError_t launch_volume_f32(const LagrangeArgs &a);
+cudaError_t launch_volume_f64(const LagrangeArgs &a);
+cudaError_t launch_vcorr_f32(const LagrangeArgs &a);
+cudaError_t launch_vcorr_f64(const LagrangeArgs &a);
+
 }  // namespace ifem

@@ -12,4 +12,7 @@ cudaError_t launch_interp_f32(const TransferArgs &a) { return interp_impl<float>
 cudaError_t launch_reduce_f32(const ReduceArgs &a) { return reduce_impl<float>(a); }
 cudaError_t launch_fluid_f32(const FluidArgs &a) { return fluid_impl<float>(a); }
 cudaError_t launch_interp_cc_f32(const TransferArgs &a, int ncomp) { return interp_cc_impl<float>(a, ncomp); }
+cudaError_t launch_ab2_f32(const LagrangeArgs &a) { return ab2_impl<float>(a); }
+cudaError_t launch_volume_f32(const LagrangeArgs &a) { return volume_impl<float>(a); }
+cudaError_t launch_vcorr_f32(const LagrangeArgs &a) { return vcorr_impl<float>(a); }
 }  // namespace ifem

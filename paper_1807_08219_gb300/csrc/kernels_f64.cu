@@ -15,4 +15,7 @@ cudaError_t launch_interp_f64(const TransferArgs &a) { return interp_impl<double
 cudaError_t launch_reduce_f64(const ReduceArgs &a) { return reduce_impl<double>(a); }
 cudaError_t launch_fluid_f64(const FluidArgs &a) { return fluid_impl<double>(a); }
 cudaError_t launch_interp_cc_f64(const TransferArgs &a, int ncomp) { return interp_cc_impl<double>(a, ncomp); }
+cudaError_t launch_ab2_f64(const LagrangeArgs &a) { return ab2_impl<double>(a); }
+cudaError_t launch_volume_f64(const LagrangeArgs &a) { return volume_impl<double>(a); }
+cudaError_t launch_vcorr_f64(const LagrangeArgs &a) { return vcorr_impl<double>(a); }
 }  // namespace ifem

@@ -6,6 +6,7 @@
 #include "common.cuh"
 #include "forces.cuh"
 #include "transfer.cuh"
+#include "lagrangian.cuh"
 
 namespace ifem {
 
@@ -208,6 +209,42 @@ cudaError_t interp_cc_impl(const TransferArgs &a, int ncomp)
     else
         interp_cc_kernel<real, 1><<<grid, 256, 0, a.stream>>>(b, a.g, a.w, (const real *)a.u, ncomp,
                                                               (const real *)a.x, (real *)a.v, (real)a.support);
+    IFEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
+template <typename real>
+cudaError_t ab2_impl(const LagrangeArgs &a)
+{
+    const long long n3 = 3 * a.b.N;
+    if (n3 == 0)
+        return cudaSuccess;
+    ab2_kernel<real><<<(unsigned)((n3 + 255) / 256), 256, 0, a.stream>>>(n3, (real *)a.x, (const real *)a.v,
+                                                                         (const real *)a.vp, (real)a.dt);
+    IFEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
+template <typename real>
+cudaError_t volume_impl(const LagrangeArgs &a)
+{
+    if (a.b.n_inst == 0)
+        return cudaSuccess;
+    volume_kernel<real><<<a.b.n_inst, kVolThreads, 0, a.stream>>>(a.b, (const real *)a.x, a.out);
+    IFEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
+template <typename real>
+cudaError_t vcorr_impl(const LagrangeArgs &a)
+{
+    if (a.b.n_inst == 0)
+        return cudaSuccess;
+    dim3 gn((a.b.max_nodes + 255) / 256, a.b.n_inst);
+    vc_alpha_kernel<real><<<gn, 256, 0, a.stream>>>(a.b, (const real *)a.x, a.alpha);
+    IFEM_LAUNCH_CHECK();
+    vc_correct_kernel<real><<<a.b.n_inst, kVolThreads, 0, a.stream>>>(a.b, (real *)a.x, a.alpha, a.V0, a.out,
+                                                                       a.status);
     IFEM_LAUNCH_CHECK();
     return cudaSuccess;
 }

@@ -37,7 +37,7 @@ EXPORTS = (
     "ifem_batch_create", "ifem_batch_destroy", "ifem_batch_nodes", "ifem_batch_instances",
     "ifem_batch_set_origins", "ifem_prepare", "ifem_compute_forces", "ifem_spread", "ifem_interpolate",
     "ifem_reduce", "ifem_step_coupling", "ifem_force_hvp", "ifem_compute_forces_noalloc",
-    "ifem_interpolate_cc", "ifem_fluid_stress_forces",
+    "ifem_interpolate_cc", "ifem_fluid_stress_forces", "ifem_ab2_update", "ifem_volumes", "ifem_volume_correct",
 )
 
 
@@ -123,6 +123,9 @@ def load(build_if_missing: bool = True):
         "ifem_compute_forces_noalloc": (i, [p, p, p, p, p]),
         "ifem_interpolate_cc": (i, [p, p, p, p, i, p, p, p]),
         "ifem_fluid_stress_forces": (i, [p, p, p, p, p, p, p, i, p]),
+        "ifem_ab2_update": (i, [p, p, p, p, p, d, p]),
+        "ifem_volumes": (i, [p, p, p, p, p]),
+        "ifem_volume_correct": (i, [p, p, p, p, p, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -299,6 +302,18 @@ def ifem_fluid_stress_forces(ctx, b, x, u, C, eta: float, beta: float, lam: floa
     prm = ifem_fluid_params(eta, beta, lam)
     return _check(ctx, load().ifem_fluid_stress_forces(ctx, b, _ptr(x), _ptr(u), _ptr(C), ctypes.byref(prm),
                                                        _ptr(F), flags, _stream(stream)))
+
+
+def ifem_ab2_update(ctx, b, x, v, v_prev, dt: float, stream=None):
+    return _check(ctx, load().ifem_ab2_update(ctx, b, _ptr(x), _ptr(v), _ptr(v_prev), float(dt), _stream(stream)))
+
+
+def ifem_volumes(ctx, b, x, vol, stream=None):
+    return _check(ctx, load().ifem_volumes(ctx, b, _ptr(x), _ptr(vol), _stream(stream)))
+
+
+def ifem_volume_correct(ctx, b, x, V0, lam=None, stream=None):
+    return _check(ctx, load().ifem_volume_correct(ctx, b, _ptr(x), _ptr(V0), _ptr(lam), _stream(stream)))
 
 
 def ifem_reduce(ctx, b, x, F, v, red, stream=None):
