@@ -346,6 +346,40 @@ def oracle_step(wl, x_local=None, kernel: int = KERNEL_PESKIN4, density: bool = 
     return out
 
 
+def area_normals(tri, x):
+    """n_k A_k of every vertex of a membrane: the unit vertex normal times the
+    mixed Voronoi area of the bending operators (Sec. "Variable Viscosity
+    Implementation" names n_k and A_k without defining them)."""
+    c = curvatures(tri, x)
+    return c["n"] * c["A"][:, None]
+
+
+def indicator_source(wl, x_local=None, kernel: int = KERNEL_PESKIN4, density: bool = True, f0=None):
+    """Source of the indicator-function Poisson equation (Sec. "Variable
+    Viscosity Implementation"): G_J = sum_k n_k A_k phi(x_J - x_k) over the
+    membrane nodes of each box, spread like a force (S*) onto the three MAC
+    lattices. Returns a list per box of (3, n, n, n)."""
+    if x_local is None:
+        x_local = wl.x_local_all()
+    x_local = _f64(x_local)
+    off = wl.node_offsets()
+    nA = np.zeros_like(x_local)
+    x_abs = np.zeros_like(x_local)
+    for ii, inst in enumerate(wl.instances):
+        a, b = off[ii], off[ii + 1]
+        tm = wl.templates[inst.tmpl]
+        if tm.kind == "membrane":
+            nA[a:b] = area_normals(tm.elems, x_local[a:b])
+        x_abs[a:b] = inst.origin[None, :] + x_local[a:b]
+    out = []
+    for bi, box in enumerate(wl.boxes):
+        rows = np.concatenate([np.arange(off[ii], off[ii + 1]) for ii, inst in enumerate(wl.instances)
+                               if inst.box == bi] or [np.zeros(0, dtype=np.int64)])
+        base = None if f0 is None else f0[bi]
+        out.append(spread(x_abs[rows], nA[rows], box.n, box.L, kernel, density, f0=base))
+    return out
+
+
 def reductions(wl, x_local, F, v, sel=None):
     """Per-particle FP64 sums: centroid c, sum F, sum (x - c) x F, sum v (correctly rounded)."""
     off = wl.node_offsets()

@@ -94,3 +94,56 @@ def test_no_correction_at_target_volume(cell):
     x = _perturbed(X, 5, 1.0)
     xc, _, lam = O.volume_correction(tri, x, O.volume(tri, x))
     assert lam == 0.0 and np.array_equal(xc, x)
+
+
+# ------------------------------------------------ indicator-function source
+def test_mixed_areas_partition_the_surface(cell):
+    """sum_k A_k equals the total triangle area (mixed Voronoi areas tile the surface)."""
+    X, tri = cell
+    x = _perturbed(X, 6, 1.0)
+    e1 = x[tri[:, 1]] - x[tri[:, 0]]
+    e2 = x[tri[:, 2]] - x[tri[:, 0]]
+    area = 0.5 * np.linalg.norm(np.cross(e1, e2), axis=1).sum()
+    assert O.curvatures(tri, x)["A"].sum() == pytest.approx(area, rel=1e-13)
+
+
+def test_area_normals_divergence_theorem_converges():
+    """sum_k (n_k A_k) . x_k -> 3 V (divergence theorem) at second order on refined spheres,
+    and sum_k n_k A_k -> 0 for the closed surface."""
+    errs = []
+    for level in (2, 3, 4):
+        X, tri = meshes.icosphere(level)
+        x = X * 0.8 + np.array([0.1, -0.3, 0.2])
+        nA = O.area_normals(tri, x)
+        V = O.volume(tri, x)
+        errs.append(abs(np.sum(nA * x) - 3.0 * V) / (3.0 * V))
+        assert np.abs(nA.sum(0)).max() <= 1e-12 * np.abs(nA).sum()
+    assert errs[1] < errs[0] / 3.0 and errs[2] < errs[1] / 3.0
+
+
+def test_indicator_source_is_the_spread_of_area_normals():
+    """Density form: the first moment sum_d h^3 sum_J G_d,J x_J,d of the source equals
+    sum_k n_k A_k . x_k (the Peskin kernel reproduces linear functions; the cell does
+    not touch the box faces), a non-zero quantity close to 3 V."""
+    import ifem_workloads as W
+    from ifem_workloads.fields import mac_offset
+    w = W.make("C2")
+    G = O.indicator_source(w)
+    off = w.node_offsets()
+    inst = w.instances[0]
+    tm = w.templates[inst.tmpl]
+    xl = w.x_local_all()[off[0]:off[1]]
+    nA = O.area_normals(tm.elems, xl)
+    xa = inst.origin[None, :] + xl
+    bx = w.boxes[0]
+    h = bx.L / bx.n
+    idx = np.arange(bx.n)
+    moment = 0.0
+    for d in range(3):
+        coord = (idx + mac_offset(d)[d]) * h
+        shape = [1, 1, 1]
+        shape[2 - d] = bx.n
+        moment += h**3 * np.sum(G[0][d] * coord.reshape(shape))
+    expect = np.sum(nA * xa)
+    assert moment == pytest.approx(expect, rel=1e-12)
+    assert expect == pytest.approx(3.0 * O.volume(tm.elems, xl), rel=0.02)
