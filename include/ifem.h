@@ -302,6 +302,19 @@ typedef struct {
 int ifem_fluid_stress_forces(ifem_ctx ctx, ifem_batch b, const void *x, const void *u, const void *C,
                              const ifem_fluid_params *p, void *F, int flags, void *stream);
 
+/* Source of the indicator-function equation lap I = div G of the variable-
+ * viscosity model (Sec. "Variable Viscosity Implementation"):
+ *   G_J = s sum_k n_k A_k phi(x_J - (origin_k + x_k)),
+ * n_k A_k the unit vertex normal times the mixed Voronoi area of membrane
+ * node k (the operators of the bending force; solid nodes contribute 0),
+ * spread onto the three MAC lattices exactly as ifem_spread spreads a force:
+ * same kernels, flags, precision and summation order (s = (n_b/L_b)^3, or 1
+ * with IFEM_SPREAD_FORCE). x: device node array; G: device grid field. Uses
+ * the batch's internal scratch: calls on one batch must not overlap on the
+ * GPU. The Poisson solve itself is not part of this library. */
+int ifem_indicator_source(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, void *G, int flags,
+                          void *stream);
+
 /* ------------------------------------------------------ Lagrangian update */
 /* Adams-Bashforth position update (Eq. Bashforth_eqn), in place:
  *   x = x + dt (3/2 v - 1/2 v_prev)

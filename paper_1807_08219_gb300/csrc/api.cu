@@ -905,6 +905,28 @@ extern "C" int ifem_volume_correct(ifem_ctx ctx, ifem_batch b, void *x, const do
     return launch_rc(ctx, e, "volume_correct");
 }
 
+extern "C" int ifem_indicator_source(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, void *G, int flags,
+                                     void *stream)
+{
+    int rc = check_call(ctx, b, g);
+    if (rc != IFEM_OK)
+        return rc;
+    if (!g || !G || (!x && b->N > 0))
+        return fail(ctx, IFEM_ERR_ARG, "indicator_source: null array or grid");
+    if (flags & ~(IFEM_SPREAD_FORCE | IFEM_SPREAD_OVERWRITE))
+        return fail(ctx, IFEM_ERR_ARG, "indicator_source: unknown flags");
+    // n_k A_k into the batch scratch (a node array), then the spread of S*
+    void *nA = b->d_bend_buf;
+    DevBatch db = dev_batch(b);
+    cudaError_t e = ctx->cfg.precision == IFEM_FP64 ? launch_area_normals_f64(db, x, nA, (cudaStream_t)stream)
+                                                    : launch_area_normals_f32(db, x, nA, (cudaStream_t)stream);
+    if ((rc = launch_rc(ctx, e, "indicator_source")) != IFEM_OK)
+        return rc;
+    if ((rc = do_bin(ctx, b, g, x, stream)) != IFEM_OK)
+        return rc;
+    return do_spread(ctx, b, g, x, nA, G, flags, stream);
+}
+
 extern "C" int ifem_interpolate_cc(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *field, int ncomp,
                                    const void *x, void *out, void *stream)
 {

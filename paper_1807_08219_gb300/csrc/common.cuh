@@ -381,5 +381,7 @@ cudaError_t launch_volume_f32(const LagrangeArgs &a);
 cudaError_t launch_volume_f64(const LagrangeArgs &a);
 cudaError_t launch_vcorr_f32(const LagrangeArgs &a);
 cudaError_t launch_vcorr_f64(const LagrangeArgs &a);
+cudaError_t launch_area_normals_f32(const DevBatch &b, const void *x, void *nA, cudaStream_t s);
+cudaError_t launch_area_normals_f64(const DevBatch &b, const void *x, void *nA, cudaStream_t s);
 
 }  // namespace ifem

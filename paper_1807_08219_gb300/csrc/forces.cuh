@@ -663,6 +663,38 @@ __global__ void bend_pass1_kernel(DevBatch b, const real *__restrict__ x, real *
     o[0] = A; o[1] = kH; o[2] = kG; o[3] = n[0]; o[4] = n[1]; o[5] = n[2];
 }
 
+// n_k A_k of every membrane node (unit normal times mixed area, from the
+// bending pass-1 operators) as a node array; solid nodes get 0. Source of
+// the indicator-function equation (Sec. "Variable Viscosity Implementation").
+template <typename real>
+__global__ void area_normal_kernel(DevBatch b, const real *__restrict__ x, real *__restrict__ nA)
+{
+    const int i = blockIdx.y;
+    const InstDev I = b.inst[i];
+    const TmplDev T = b.tmpl[I.tmpl];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= T.n_nodes)
+        return;
+    const long long N = b.N;
+    const long long node = I.node_off + k;
+    if (T.kind != 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            nA[a * N + node] = real(0);
+        return;
+    }
+    auto ld = [&](int v, real p[3]) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            p[a] = x[a * N + I.node_off + v];
+    };
+    real A, kH, kG, n[3];
+    bend_vertex_pass1<real>(T, k, ld, A, kH, kG, n);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        nA[a * N + node] = n[a] * A;
+}
+
 // F = F_el + F_be (one add per component).
 template <typename real>
 __global__ void bend_pass2_kernel(DevBatch b, const real *__restrict__ x, const real *__restrict__ bb,

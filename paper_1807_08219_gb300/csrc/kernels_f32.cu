@@ -15,4 +15,8 @@ cudaError_t launch_interp_cc_f32(const TransferArgs &a, int ncomp) { return inte
 cudaError_t launch_ab2_f32(const LagrangeArgs &a) { return ab2_impl<float>(a); }
 cudaError_t launch_volume_f32(const LagrangeArgs &a) { return volume_impl<float>(a); }
 cudaError_t launch_vcorr_f32(const LagrangeArgs &a) { return vcorr_impl<float>(a); }
+cudaError_t launch_area_normals_f32(const DevBatch &b, const void *x, void *nA, cudaStream_t s)
+{
+    return area_normals_impl<float>(b, x, nA, s);
+}
 }  // namespace ifem

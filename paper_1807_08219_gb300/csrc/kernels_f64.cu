@@ -18,4 +18,8 @@ cudaError_t launch_interp_cc_f64(const TransferArgs &a, int ncomp) { return inte
 cudaError_t launch_ab2_f64(const LagrangeArgs &a) { return ab2_impl<double>(a); }
 cudaError_t launch_volume_f64(const LagrangeArgs &a) { return volume_impl<double>(a); }
 cudaError_t launch_vcorr_f64(const LagrangeArgs &a) { return vcorr_impl<double>(a); }
+cudaError_t launch_area_normals_f64(const DevBatch &b, const void *x, void *nA, cudaStream_t s)
+{
+    return area_normals_impl<double>(b, x, nA, s);
+}
 }  // namespace ifem

@@ -249,4 +249,15 @@ cudaError_t vcorr_impl(const LagrangeArgs &a)
     return cudaSuccess;
 }
 
+template <typename real>
+cudaError_t area_normals_impl(const DevBatch &b, const void *x, void *nA, cudaStream_t s)
+{
+    if (b.n_inst == 0)
+        return cudaSuccess;
+    dim3 gn((b.max_nodes + 255) / 256, b.n_inst);
+    area_normal_kernel<real><<<gn, 256, 0, s>>>(b, (const real *)x, (real *)nA);
+    IFEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
 }  // namespace ifem

@@ -38,6 +38,7 @@ EXPORTS = (
     "ifem_batch_set_origins", "ifem_prepare", "ifem_compute_forces", "ifem_spread", "ifem_interpolate",
     "ifem_reduce", "ifem_step_coupling", "ifem_force_hvp", "ifem_compute_forces_noalloc",
     "ifem_interpolate_cc", "ifem_fluid_stress_forces", "ifem_ab2_update", "ifem_volumes", "ifem_volume_correct",
+    "ifem_indicator_source",
 )
 
 
@@ -126,6 +127,7 @@ def load(build_if_missing: bool = True):
         "ifem_ab2_update": (i, [p, p, p, p, p, d, p]),
         "ifem_volumes": (i, [p, p, p, p, p]),
         "ifem_volume_correct": (i, [p, p, p, p, p, p]),
+        "ifem_indicator_source": (i, [p, p, p, p, p, i, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -302,6 +304,10 @@ def ifem_fluid_stress_forces(ctx, b, x, u, C, eta: float, beta: float, lam: floa
     prm = ifem_fluid_params(eta, beta, lam)
     return _check(ctx, load().ifem_fluid_stress_forces(ctx, b, _ptr(x), _ptr(u), _ptr(C), ctypes.byref(prm),
                                                        _ptr(F), flags, _stream(stream)))
+
+
+def ifem_indicator_source(ctx, b, g, x, G, flags: int = 0, stream=None):
+    return _check(ctx, load().ifem_indicator_source(ctx, b, g, _ptr(x), _ptr(G), flags, _stream(stream)))
 
 
 def ifem_ab2_update(ctx, b, x, v, v_prev, dt: float, stream=None):
