@@ -228,6 +228,66 @@ def cpu_baseline_sample(wl):
                       f"interp + sums), single thread, {sum(ts):.1f} s"}
 
 
+def time_extras(wl, I, torch, dev, flush, T, reps=20, warm=3):
+    """CUDA-event times of the Lagrangian-update and fluid-stress entry points
+    on the resident workload (FP32, same context kind as the step), each with
+    its algorithmic bytes: every node array read or written once, grid values
+    read (or read and written) once over the touched footprint."""
+    import math
+    N = wl.n_nodes
+    n_solid = int(sum(wl.templates[i.tmpl].n_nodes for i in wl.instances if wl.templates[i.tmpl].kind == "solid"))
+    cp = I.Coupler(wl, precision=I.IFEM_FP32, scatter=I.IFEM_SCATTER_ATOMIC, tile=16)
+    s = torch.cuda.Stream(device=dev)
+    x0 = cp.nodes_to_device(wl.x_local_all(np.float32))
+    x = x0.clone()
+    v = torch.randn((3, N), device=dev) * 0.1
+    vp = torch.randn((3, N), device=dev) * 0.1
+    F = cp.empty_nodes()
+    # cell-centred conformation field I + smooth perturbation, 6 components per box
+    parts = []
+    for bx in wl.boxes:
+        c = (torch.arange(bx.n, device=dev, dtype=torch.float32) + 0.5) * (2 * math.pi / bx.n)
+        z, y, xg = torch.meshgrid(c, c, c, indexing="ij")
+        base = 0.05 * torch.cos(xg + 2 * y - z)
+        parts.append(torch.stack([1 + base, 1 - base, 1 + 0.5 * base, 0.3 * base, -0.2 * base, 0.1 * base]).reshape(-1))
+    field = torch.cat(parts)
+    Cn = torch.empty((6, N), device=dev)
+    G = cp.zeros_grid()
+    vol = torch.empty(len(wl.instances), dtype=torch.float64, device=dev)
+    I.ifem_volumes(cp.ctx, cp.batch, x0, vol, s)
+    V0 = vol.clone()
+    lam = torch.empty_like(vol)
+    calls = {
+        "interp_cc6": (lambda: I.ifem_interpolate_cc(cp.ctx, cp.batch, cp.grid, field, 6, x0, Cn, s),
+                       12 * N + 24 * N + 6 * 4 * (T // 3)),
+        "fluid_stress_forces": (lambda: I.ifem_fluid_stress_forces(cp.ctx, cp.batch, x0, v, Cn, 1.0, 0.5, 1.0, F,
+                                                                   0, s), 12 * N + 48 * n_solid),
+        "ab2_update": (lambda: I.ifem_ab2_update(cp.ctx, cp.batch, x, v, vp, 1e-4, s), 48 * N),
+        "volumes": (lambda: I.ifem_volumes(cp.ctx, cp.batch, x0, vol, s), 12 * N),
+        "volume_correct": (lambda: I.ifem_volume_correct(cp.ctx, cp.batch, x, V0, lam, s), 24 * N + 24 * N),
+        "indicator_source": (lambda: I.ifem_indicator_source(cp.ctx, cp.batch, cp.grid, x0, G, 0, s),
+                             12 * N + 8 * T),
+    }
+    out = {}
+    for name, (call, nbytes) in calls.items():
+        ts = []
+        for it in range(warm + reps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            call()
+            e1.record(s)
+            e1.synchronize()
+            if it >= warm:
+                ts.append(e0.elapsed_time(e1))
+        ms = float(np.mean(ts))
+        out[name] = {"ms": ms, "nodes_per_s": N / (ms * 1e-3), "algorithmic_bytes": int(nbytes),
+                     "gbs": nbytes / (ms * 1e-3) / 1e9}
+    I.ifem_sync_status(cp.ctx)
+    cp.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -238,6 +298,7 @@ def main():
     ap.add_argument("--tile", type=int, default=0, help="tile edge; 0 = autotune (ifem_prepare)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip timing the Lagrangian-update entry points")
     ap.add_argument("--workload", default="C4", choices=sorted(WORKLOADS),
                     help="C4 (default, the headline suspension) or C5 (64 mixed boxes)")
     args = ap.parse_args()
@@ -365,6 +426,9 @@ def main():
             e2e.append(e0.elapsed_time(e1))
     e2e_ms = max_over_ranks([float(np.mean(e2e))], dev, dist)[0]
 
+    # Lagrangian update, fluid-stress and indicator entry points (reported beside)
+    extras = None if args.no_extras else time_extras(wl, I, torch, dev, flush, T)
+
     # FP64 deterministic GPU path on the same workload (reported beside)
     fp64 = None
     if not args.no_fp64:
@@ -422,6 +486,7 @@ def main():
         "e2e": {"value": job_throughput(N, world, e2e_ms), "unit": "nodes/s", "h2d_bytes_per_step": 12 * N,
                 "d2h_bytes_per_step": 12 * N + 8 * red.numel()},
         "fp64": fp64,
+        "extras": extras,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": ck,
         "wall_s_timed": wall,

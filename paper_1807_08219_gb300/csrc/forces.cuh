@@ -386,8 +386,8 @@ __global__ void elem_force_kernel(DevBatch b, const real *__restrict__ x, const 
 }
 
 // Thread per (instance, node): F = sum over incident (element, vertex) in
-// ascending element order, starting from 0: acc = acc + f (ADD: F = F + acc).
-template <typename real, bool ADD = false>
+// ascending element order, starting from 0: acc = acc + f.
+template <typename real>
 __global__ void node_gather_kernel(DevBatch b, const real *__restrict__ ebuf, real *__restrict__ F)
 {
     const int i = blockIdx.y;
@@ -406,10 +406,8 @@ __global__ void node_gather_kernel(DevBatch b, const real *__restrict__ ebuf, re
     }
     const long long N = b.N;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        real *p = F + a * N + I.node_off + k;
-        *p = ADD ? *p + acc[a] : acc[a];
-    }
+    for (int a = 0; a < 3; ++a)
+        F[a * N + I.node_off + k] = acc[a];
 }
 
 // ------------------------------------------------------------ fluid stress
@@ -483,9 +481,9 @@ __device__ __forceinline__ void tet_fluid_force(real eta, real cp, const real *M
         f[0][i] = -((f[1][i] + f[2][i]) + f[3][i]);
 }
 
-// Thread per (instance, element): the element's fluid-stress nodal forces
-// into elem_buf (zeros for membrane elements, which carry no fluid stress
-// in the paper's thin-shell model), then node_gather_kernel sums them.
+// Thread per (instance, element) of a solid: the element's fluid-stress
+// nodal forces into elem_buf; fluid_gather_kernel then sums them per node.
+// Membranes carry no fluid stress in the paper's thin-shell model.
 template <typename real>
 __global__ void fluid_elem_kernel(DevBatch b, const real *__restrict__ x, const real *__restrict__ u,
                                   const real *__restrict__ C, real eta, real cp, real *__restrict__ ebuf)
@@ -495,13 +493,9 @@ __global__ void fluid_elem_kernel(DevBatch b, const real *__restrict__ x, const 
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= T.n_elems)
         return;
+    if (T.kind == 0)
+        return;   // membranes: no fluid stress (fluid_gather_kernel writes their zeros)
     real *out = ebuf + (I.elem_off + e) * 12;
-    if (T.kind == 0) {
-#pragma unroll
-        for (int i = 0; i < 12; ++i)
-            out[i] = real(0);
-        return;
-    }
     const long long N = b.N;
     real xs[4][3], us[4][3], Cs[4][6], f[4][3];
 #pragma unroll
@@ -661,6 +655,34 @@ __global__ void bend_pass1_kernel(DevBatch b, const real *__restrict__ x, real *
     bend_vertex_pass1<real>(T, k, ld, A, kH, kG, n);
     real *o = bb + 6LL * (I.node_off + k);
     o[0] = A; o[1] = kH; o[2] = kG; o[3] = n[0]; o[4] = n[1]; o[5] = n[2];
+}
+
+// Node sums of the fluid-stress element buffer for solids (ascending element
+// order from 0, as node_gather_kernel); membrane nodes get 0 (ADD: unchanged).
+template <typename real, bool ADD>
+__global__ void fluid_gather_kernel(DevBatch b, const real *__restrict__ ebuf, real *__restrict__ F)
+{
+    const InstDev I = b.inst[blockIdx.y];
+    const TmplDev T = b.tmpl[I.tmpl];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= T.n_nodes || (ADD && T.kind == 0))
+        return;
+    real acc[3] = {real(0), real(0), real(0)};
+    if (T.kind != 0) {
+        for (int q = T.inc_off[k]; q < T.inc_off[k + 1]; ++q) {
+            const int code = T.inc_idx[q];
+            const real *src = ebuf + (I.elem_off + (code >> 2)) * 12 + 3 * (code & 3);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                acc[a] = acc[a] + src[a];
+        }
+    }
+    const long long N = b.N;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        real *p = F + a * N + I.node_off + k;
+        *p = ADD ? *p + acc[a] : acc[a];
+    }
 }
 
 // n_k A_k of every membrane node (unit normal times mixed area, from the

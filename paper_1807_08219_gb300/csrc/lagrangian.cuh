@@ -41,7 +41,8 @@ __device__ __forceinline__ void load_node_d(const real *x, long long N, long lon
 constexpr int kVolThreads = 256;
 
 // Block per instance: membranes V = (1/18) sum_faces [a.(b x c) + b.(c x a)
-// + c.(a x b)] (the polyhedron formula), solids V = sum_tets det(Ds)/6.
+// + c.(a x b)] (the polyhedron formula; the three terms are equal, so
+// V = 1/6 sum a.(b x c)), solids V = sum_tets det(Ds)/6.
 template <typename real>
 __global__ void __launch_bounds__(kVolThreads) volume_kernel(DevBatch b, const real *__restrict__ x,
                                                              double *__restrict__ vol)
@@ -53,16 +54,13 @@ __global__ void __launch_bounds__(kVolThreads) volume_kernel(DevBatch b, const r
     double s = 0.0;
     for (int e = threadIdx.x; e < T.n_elems; e += blockDim.x) {
         if (T.kind == 0) {
+            // the three cyclic triple products of the formula are equal: one
+            // per face, V = 1/6 sum a.(b x c)
             double p[3][3], t[3];
             for (int c = 0; c < 3; ++c)
                 load_node_d(x, N, I.node_off + T.elems[3 * e + c], p[c]);
             cross3d(p[1], p[2], t);
-            double acc = dot3d(p[0], t);
-            cross3d(p[2], p[0], t);
-            acc += dot3d(p[1], t);
-            cross3d(p[0], p[1], t);
-            acc += dot3d(p[2], t);
-            s += acc;
+            s += dot3d(p[0], t);
         } else {
             double p[4][3], Ds[3][3];
             for (int c = 0; c < 4; ++c)
@@ -75,7 +73,7 @@ __global__ void __launch_bounds__(kVolThreads) volume_kernel(DevBatch b, const r
     }
     const double r = block_sum<kVolThreads>(s, sh);
     if (threadIdx.x == 0)
-        vol[blockIdx.x] = T.kind == 0 ? r / 18.0 : r;
+        vol[blockIdx.x] = T.kind == 0 ? r / 6.0 : r;
 }
 
 // Thread per (instance, node) of a membrane: alpha_I = -(1/12) sum over the
@@ -111,7 +109,9 @@ __global__ void vc_alpha_kernel(DevBatch b, const real *__restrict__ x, double *
 // Block per instance of a membrane: the cubic A L^3 + B L^2 + C L + D = 0 of
 // the volume correction with the paper's cyclic sums (A = (1/18) sum
 // alpha.(alpha x alpha), B = (1/6) sum x.(alpha x alpha), C = (1/6) sum
-// alpha.(x x x), D = V(x) - V0, FP64 block trees), Lambda by Newton from 0
+// alpha.(x x x), D = V(x) - V0, FP64 block trees; for A and V the three
+// cyclic terms are equal and one is taken, times 3, and C is evaluated as
+// -2 sum |alpha_I|^2, equal to it since alpha_I = -(1/2) grad_I V), Lambda by Newton from 0
 // (|step| <= 1e-15 max(1, |L|), at most 100 steps; the root the oracle
 // takes), then x_I = x_I + Lambda alpha_I. Solids: lambda = 0, x unchanged.
 // status ST_DOMAIN counts instances whose Newton failed (x left unchanged).
@@ -144,22 +144,29 @@ __global__ void __launch_bounds__(kVolThreads) vc_correct_kernel(DevBatch b, rea
             q[c][1] = al[1];
             q[c][2] = al[2];
         }
-        // cyclic (a, b, c), (b, c, a), (c, a, b)
+        // cyclic (a, b, c), (b, c, a), (c, a, b): B takes all three terms;
+        // the three terms of A and of V are equal, so those take one (1/6)
+        double xx[3], qq[3];
+        cross3d(p[1], p[2], xx);
+        sV += dot3d(p[0], xx);
         for (int c = 0; c < 3; ++c) {
             const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
-            double xx[3], qq[3];
-            cross3d(p[c1], p[c2], xx);
             cross3d(q[c1], q[c2], qq);
-            sV += dot3d(p[c], xx);
-            sC += dot3d(q[c], xx);
             sB += dot3d(p[c], qq);
-            sA += dot3d(q[c], qq);
+            if (c == 0)
+                sA += dot3d(q[0], qq);
         }
     }
-    const double A = block_sum<kVolThreads>(sA, sh) / 18.0;
+    // C = 1/6 sum alpha.(x x x) (cyclic) = sum_I alpha_I . grad_I V = -2 sum_I |alpha_I|^2,
+    // since alpha_I = -(1/2) grad_I V exactly
+    for (int k = threadIdx.x; k < T.n_nodes; k += blockDim.x) {
+        const double *al = alpha + 3 * (I.node_off + k);
+        sC += al[0] * al[0] + al[1] * al[1] + al[2] * al[2];
+    }
+    const double A = block_sum<kVolThreads>(sA, sh) / 6.0;
     const double B = block_sum<kVolThreads>(sB, sh) / 6.0;
-    const double C = block_sum<kVolThreads>(sC, sh) / 6.0;
-    const double D = block_sum<kVolThreads>(sV, sh) / 18.0 - V0[blockIdx.x];
+    const double C = -2.0 * block_sum<kVolThreads>(sC, sh);
+    const double D = block_sum<kVolThreads>(sV, sh) / 6.0 - V0[blockIdx.x];
     if (threadIdx.x == 0) {
         double L = 0.0;
         bool ok = false;

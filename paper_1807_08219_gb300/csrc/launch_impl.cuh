@@ -189,9 +189,9 @@ cudaError_t fluid_impl(const FluidArgs &a)
                                                       (real)a.eta, (real)a.cp, ebuf);
     IFEM_LAUNCH_CHECK();
     if (a.add)
-        node_gather_kernel<real, true><<<gn, blk, 0, a.stream>>>(b, ebuf, (real *)a.F);
+        fluid_gather_kernel<real, true><<<gn, blk, 0, a.stream>>>(b, ebuf, (real *)a.F);
     else
-        node_gather_kernel<real, false><<<gn, blk, 0, a.stream>>>(b, ebuf, (real *)a.F);
+        fluid_gather_kernel<real, false><<<gn, blk, 0, a.stream>>>(b, ebuf, (real *)a.F);
     IFEM_LAUNCH_CHECK();
     return cudaSuccess;
 }
@@ -202,7 +202,7 @@ cudaError_t interp_cc_impl(const TransferArgs &a, int ncomp)
     const DevBatch &b = a.b;
     if (b.n_inst == 0 || b.N == 0)
         return cudaSuccess;
-    unsigned grid = (unsigned)((b.N + 255) / 256);
+    unsigned grid = (unsigned)((b.N * ncomp + 255) / 256);
     if (a.kernel == 0)
         interp_cc_kernel<real, 0><<<grid, 256, 0, a.stream>>>(b, a.g, a.w, (const real *)a.u, ncomp,
                                                               (const real *)a.x, (real *)a.v, (real)a.support);

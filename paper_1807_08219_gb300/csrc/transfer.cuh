@@ -1391,26 +1391,29 @@ __global__ void __launch_bounds__(256) interp_kernel(DevBatch b, DevGrid g, DevW
 // ------------------------------------------- interpolation, cell-centred
 // S of a cell-centred field with ncomp components (the conformation tensor
 // C_J of Sec. "Interpolation Scheme"): all components at ((i,j,k) + 1/2) h.
-// Thread per node; the stencil weights are computed once and applied to
-// every component in the oracle's order: acc = acc + w * c_J from 0,
-// z-outer, x-inner, w = (phi_x * phi_y) * phi_z. Field layout: box b holds
-// ncomp blocks of n_b^3 values from (grid_off_b / 3) * ncomp; out: ncomp
-// rows of N.
+// Thread per (node, component), component-major (neighbouring threads are
+// neighbouring nodes of one component). FP64 in the oracle's order:
+// acc = acc + w * c_J from 0, z-outer, x-inner, w = (phi_x * phi_y) * phi_z;
+// FP32 Peskin in separable form (x rows, then y, then z). Field layout: box b
+// holds ncomp blocks of n_b^3 values from (grid_off_b / 3) * ncomp; out:
+// ncomp rows of N.
 template <typename real, int KER>
 __global__ void __launch_bounds__(256) interp_cc_kernel(DevBatch b, DevGrid g, DevWork w,
                                                         const real *__restrict__ field, int ncomp,
                                                         const real *__restrict__ x, real *__restrict__ out,
                                                         real support)
 {
-    const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (node >= b.N)
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long N = b.N;
+    if (idx >= N * ncomp)
         return;
+    const int q = (int)(idx / N);
+    const long long node = idx - q * N;
     const InstDev I = b.inst[b.node_inst[node]];
     const BoxDev B = g.boxes[I.box];
-    const long long N = b.N;
     const int n = B.n;
     const long long n3 = (long long)n * n * n;
-    const real *fb = field + (B.grid_off / 3) * ncomp;
+    const real *cq = field + (B.grid_off / 3) * ncomp + q * n3;
     real xl[3];
     bool finite = true;
 #pragma unroll
@@ -1419,12 +1422,44 @@ __global__ void __launch_bounds__(256) interp_cc_kernel(DevBatch b, DevGrid g, D
         finite = finite && isfinite(xl[a]);
     }
     if (!finite) {
-        status_add(w.status, ST_DOMAIN, 1);
-        for (int q = 0; q < ncomp; ++q)
-            out[q * N + node] = xl[0] + xl[1] + xl[2];
+        if (q == 0)
+            status_add(w.status, ST_DOMAIN, 1);
+        out[q * N + node] = xl[0] + xl[1] + xl[2];
         return;
     }
-    if constexpr (KER == 0) {
+    real acc = real(0);
+    if constexpr (KER == 0 && std::is_same<real, float>::value) {
+        float ph[3][4];
+        int ix[4], iy[4], iz[4];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int I0;
+            const float s = LatCoord<float>::get(I, B, a, xl[a], 0.5f, I0);
+            const int base = wrap_near(I0 + peskin_axis_fast(s, ph[a]), n);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                int id = base + m;
+                id -= id >= n ? n : 0;
+                if (a == 0) ix[m] = id;
+                else if (a == 1) iy[m] = id;
+                else iz[m] = id;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float accz = 0.f;
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb) {
+                const float *row = cq + ((long long)iz[c] * n + iy[bb]) * n;
+                float accy = ph[0][0] * __ldg(row + ix[0]);
+#pragma unroll
+                for (int a = 1; a < 4; ++a)
+                    accy += ph[0][a] * __ldg(row + ix[a]);
+                accz += ph[1][bb] * accy;
+            }
+            acc += ph[2][c] * accz;
+        }
+    } else if constexpr (KER == 0) {
         real ph[3][4];
         int ix[4], iy[4], iz[4];
 #pragma unroll
@@ -1440,20 +1475,15 @@ __global__ void __launch_bounds__(256) interp_cc_kernel(DevBatch b, DevGrid g, D
                 else iz[m] = wi;
             }
         }
-        for (int q = 0; q < ncomp; ++q) {
-            const real *cq = fb + q * n3;
-            real acc = real(0);
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
+        for (int c = 0; c < 4; ++c)
 #pragma unroll
-                for (int bb = 0; bb < 4; ++bb)
+            for (int bb = 0; bb < 4; ++bb)
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        real wgt = (ph[0][a] * ph[1][bb]) * ph[2][c];
-                        acc = acc + wgt * cq[((long long)iz[c] * n + iy[bb]) * n + ix[a]];
-                    }
-            out[q * N + node] = acc;
-        }
+                for (int a = 0; a < 4; ++a) {
+                    real wgt = (ph[0][a] * ph[1][bb]) * ph[2][c];
+                    acc = acc + wgt * cq[((long long)iz[c] * n + iy[bb]) * n + ix[a]];
+                }
     } else {
         real s[3];
         int I0[3];
@@ -1463,29 +1493,25 @@ __global__ void __launch_bounds__(256) interp_cc_kernel(DevBatch b, DevGrid g, D
         int base[3];
         real wt[27];
         if (!mls_weights<real>(s, support, base, wt)) {
-            status_add(w.status, ST_DOMAIN, 1);
-            for (int q = 0; q < ncomp; ++q)
-                out[q * N + node] = real(0);
+            if (q == 0)
+                status_add(w.status, ST_DOMAIN, 1);
+            out[q * N + node] = real(0);
             return;
         }
-        for (int q = 0; q < ncomp; ++q) {
-            const real *cq = fb + q * n3;
-            real acc = real(0);
-            int J = 0;
+        int J = 0;
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
-                for (int bb = 0; bb < 3; ++bb)
+            for (int bb = 0; bb < 3; ++bb)
 #pragma unroll
-                    for (int a = 0; a < 3; ++a, ++J) {
-                        long long gi = ((long long)wrapi((long long)I0[2] + base[2] + c, n) * n
-                                        + wrapi((long long)I0[1] + base[1] + bb, n)) * n
-                                       + wrapi((long long)I0[0] + base[0] + a, n);
-                        acc = acc + wt[J] * cq[gi];
-                    }
-            out[q * N + node] = acc;
-        }
+                for (int a = 0; a < 3; ++a, ++J) {
+                    long long gi = ((long long)wrapi((long long)I0[2] + base[2] + c, n) * n
+                                    + wrapi((long long)I0[1] + base[1] + bb, n)) * n
+                                   + wrapi((long long)I0[0] + base[0] + a, n);
+                    acc = acc + wt[J] * cq[gi];
+                }
     }
+    out[q * N + node] = acc;
 }
 
 // ------------------------------------------------------------- reductions
