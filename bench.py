@@ -44,7 +44,7 @@ REF_BUDGET_S = 150.0   # --impl reference: warm-up + timed oracle steps
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the current kernels on the C4 suspension (profiles/*_c4_fp32.md),
 # reported for that workload only; set an entry to None when its kernel changes.
-NCU_TRAFFIC = {"spread+interp": None, "spread": None, "interp": None, "forces": None, "bin": None}
+NCU_TRAFFIC = {"spread+interp": 462.2e6, "spread": None, "interp": None, "forces": None, "bin": None}
 
 
 def peaks():
