@@ -1090,7 +1090,8 @@ extern "C" int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const
 }
 
 // Tile autotuner: time binning + spreading + interpolation of the batch at
-// its current positions x for each candidate tile edge (CUDA events on
+// its current positions x for each candidate tile edge, with the transfer
+// launches the step uses (the fused one where it fuses) (CUDA events on
 // `stream`, best of two after one warm-up run) and keep the fastest. Forces
 // for the spread are the batch's own (computed once); the velocity field is
 // zero (the gathers cost the same for any values). Temporary buffers are
@@ -1138,8 +1139,13 @@ static int autotune(ifem_ctx ctx, ifem_batch b, const void *x, void *stream)
         float tmin = 1e30f;
         for (int rep = 0; rep < 3 && rc == IFEM_OK; ++rep) {
             cudaEventRecord(e0, s);
-            if ((rc = do_bin(ctx, b, g, x, stream)) == IFEM_OK && (rc = do_spread(ctx, b, g, x, F, f, 0, stream)) == IFEM_OK)
-                rc = do_interp(ctx, b, u, x, v, stream);
+            if ((rc = do_bin(ctx, b, g, x, stream)) == IFEM_OK) {
+                // the transfer launches the step will use (fused where it fuses)
+                if (use_halo(ctx))
+                    rc = do_spread_interp(ctx, b, g, x, F, u, f, v, 0, stream);
+                else if ((rc = do_spread(ctx, b, g, x, F, f, 0, stream)) == IFEM_OK)
+                    rc = do_interp(ctx, b, u, x, v, stream);
+            }
             cudaEventRecord(e1, s);
             float ms = 0.f;
             if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
