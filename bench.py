@@ -45,6 +45,10 @@ REF_BUDGET_S = 150.0   # --impl reference: warm-up + timed oracle steps
 # ncu capture of the current kernels on the C4 suspension (profiles/*_c4_fp32.md),
 # reported for that workload only; set an entry to None when its kernel changes.
 NCU_TRAFFIC = {"spread+interp": 462.2e6, "spread": None, "interp": None, "forces": None, "bin": None}
+# The unit that bounds each kernel in that capture and its fraction of peak (context for the HBM
+# fraction: the fused transfer kernel is limited by the L1 load/store pipe, not by DRAM).
+NCU_LIMITER = {"spread+interp": ("l1tex load/store data-pipe wavefronts", 0.841),
+               "forces": ("shared-memory wavefronts", 0.598)}
 
 
 def peaks():
@@ -480,7 +484,10 @@ def main():
         "stage_ms": stage_ms,
         "touched_values": T, "pairs": P,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": NCU_TRAFFIC.get(dom) if args.workload == "C4" else None, "peak_kind": peak_kind,
+                     "frac": achieved / hbm, "traffic": NCU_TRAFFIC.get(dom) if args.workload == "C4" else None,
+                     "limiter": ({"unit": NCU_LIMITER[dom][0], "frac_of_peak": NCU_LIMITER[dom][1],
+                                  "source": "ncu capture on this workload (profiles/)"}
+                                 if args.workload == "C4" and dom in NCU_LIMITER else None), "peak_kind": peak_kind,
                      "algorithmic_bytes": ab[dom]},
         "cpu_baseline": cpu,
         "e2e": {"value": job_throughput(N, world, e2e_ms), "unit": "nodes/s", "h2d_bytes_per_step": 12 * N,
