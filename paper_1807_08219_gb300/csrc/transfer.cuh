@@ -1098,7 +1098,7 @@ __global__ void __launch_bounds__(256, 6) interp_direct_kernel(DevBatch b, DevGr
 // f = f + w*g, w = (phi_x*phi_y)*phi_z, g = F*scale. This is the oracle's
 // per-value summation order, so the result is bit-identical.
 constexpr int kDetThreads = 256;
-constexpr int kDetCells = 8;     // owned values per thread and lattice: vol <= 2048
+constexpr int kDetCells = 4;     // owned values per thread and lattice (1024 per chunk; 2 CTAs per SM)
 constexpr int kDetChunk = 32;    // candidates staged per round
 
 template <int KER>
@@ -1121,7 +1121,7 @@ struct DetCand<1> {
 };
 
 template <int KER>
-__global__ void __launch_bounds__(kDetThreads) spread_det_kernel(DevBatch b, DevGrid g, DevWork w,
+__global__ void __launch_bounds__(kDetThreads, 2) spread_det_kernel(DevBatch b, DevGrid g, DevWork w,
                                                                  const double *__restrict__ x,
                                                                  const double *__restrict__ F,
                                                                  double *__restrict__ f, int density,
