@@ -113,7 +113,7 @@ extern "C" int ifem_ctx_create(const ifem_config *cfg, ifem_ctx *out)
             ifem_ctx_destroy(ctx);
             return IFEM_ERR_CUDA;
         }
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 5; ++i)
         if (cudaEventCreateWithFlags(&ctx->fork[i], cudaEventDisableTiming) != cudaSuccess) {
             ifem_ctx_destroy(ctx);
             return IFEM_ERR_CUDA;
@@ -135,7 +135,7 @@ extern "C" int ifem_ctx_destroy(ifem_ctx ctx)
     for (int i = 0; i < 6; ++i)
         if (ctx->ev[i])
             cudaEventDestroy(ctx->ev[i]);
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 5; ++i)
         if (ctx->fork[i])
             cudaEventDestroy(ctx->fork[i]);
     for (int i = 0; i < 2; ++i)
@@ -797,9 +797,10 @@ static int do_interp(ifem_ctx ctx, ifem_batch b, const void *u, const void *x, v
 }
 
 static int do_reduce(ifem_ctx ctx, ifem_batch b, const void *x, const void *F, const void *v, double *red,
-                     void *stream)
+                     void *stream, int parts = 3)
 {
     ReduceArgs a{};
+    a.parts = parts;
     a.b = dev_batch(b);
     a.g = dev_grid(b);
     a.w = b->ws.w;
@@ -1043,9 +1044,10 @@ extern "C" int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const
         return IFEM_OK;
     }
     // fork-join over the context's two auxiliary streams (also inside stream
-    // capture): forces run beside binning, interpolation beside spreading
-    //   s:    bin ----------- wait(forces) spread  wait(interp) reduce
-    //   aux0: forces -------/
+    // capture): forces run beside binning, interpolation beside spreading,
+    // and the x/F sums (which need only the forces) beside the transfers
+    //   s:    bin ----------- wait(forces) spread  wait(interp) wait(sums) sums of v, boxes
+    //   aux0: forces -------/ sums of x, F -----------------------/
     //   aux1:       wait(bin) interp -------------/
     // (with the fused spread + interpolation the aux1 branch is absent)
     const bool fused = use_halo(ctx) != 0;
@@ -1061,6 +1063,13 @@ extern "C" int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const
         return rc;
     if ((e = cudaEventRecord(ctx->fork[1], ctx->aux[0])) != cudaSuccess)
         return launch_rc(ctx, e, "step_coupling fork");
+    // the x/F sums need only the forces: they run on aux0 beside the transfers
+    if (red) {
+        if ((rc = do_reduce(ctx, b, x, F, v, red, ctx->aux[0], 1)) != IFEM_OK)
+            return rc;
+        if ((e = cudaEventRecord(ctx->fork[4], ctx->aux[0])) != cudaSuccess)
+            return launch_rc(ctx, e, "step_coupling fork");
+    }
     if ((rc = do_bin(ctx, b, g, x, stream)) != IFEM_OK)
         return rc;
     if (!fused) {
@@ -1084,8 +1093,12 @@ extern "C" int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const
         if ((e = cudaStreamWaitEvent(s, ctx->fork[3], 0)) != cudaSuccess)
             return launch_rc(ctx, e, "step_coupling join");
     }
-    if (red && (rc = do_reduce(ctx, b, x, F, v, red, stream)) != IFEM_OK)
-        return rc;
+    if (red) {
+        if ((e = cudaStreamWaitEvent(s, ctx->fork[4], 0)) != cudaSuccess)
+            return launch_rc(ctx, e, "step_coupling join");
+        if ((rc = do_reduce(ctx, b, x, F, v, red, stream, 2)) != IFEM_OK)
+            return rc;
+    }
     return IFEM_OK;
 }
 

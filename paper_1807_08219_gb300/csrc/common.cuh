@@ -328,6 +328,7 @@ struct ReduceArgs {
     const void *F;
     const void *v;
     double *red;
+    int parts;        // 1: per-particle x/F sums; 2: per-particle sum v and the per-box sums; 3: all
     cudaStream_t stream;
 };
 

@@ -168,9 +168,12 @@ cudaError_t interp_impl(const TransferArgs &a)
 template <typename real>
 cudaError_t reduce_impl(const ReduceArgs &a)
 {
-    const unsigned blocks = (unsigned)(a.b.n_inst + 3 * a.g.n_boxes);
+    const int parts = a.parts ? a.parts : 3;
+    const unsigned blocks = (unsigned)(a.b.n_inst + ((parts & 2) ? 3 * a.g.n_boxes : 0));
+    if (blocks == 0)
+        return cudaSuccess;
     reduce_kernel<real><<<blocks, kReduceThreads, 0, a.stream>>>(a.b, a.g, a.w.red_tile, (const real *)a.x,
-                                                               (const real *)a.F, (const real *)a.v, a.red);
+                                                               (const real *)a.F, (const real *)a.v, a.red, parts);
     IFEM_LAUNCH_CHECK();
     return cudaSuccess;
 }

@@ -1542,6 +1542,9 @@ __device__ inline double block_sum(double v, double *sh)
 // sum (x - c) x F = sum x x F - c x sum F.
 // Blocks [n_inst, n_inst + 3 n_boxes): box b, lattice d -- h^3 * sum of the
 // values the last spread added, from the per-tile FP64 partials in tile order.
+// parts selects what one launch writes: 1 the x/F sums (centroid, sum F,
+// torque: entries 0..8), 2 sum v (entries 9..11) and the box blocks, 3 all;
+// the sums of one quantity do not depend on parts.
 constexpr int kReduceThreads = 256;
 
 template <typename real>
@@ -1549,7 +1552,8 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(DevBatch b, DevG
                                                                const double *__restrict__ red_tile,
                                                                const real *__restrict__ x,
                                                                const real *__restrict__ F,
-                                                               const real *__restrict__ v, double *__restrict__ red)
+                                                               const real *__restrict__ v, double *__restrict__ red,
+                                                               int parts)
 {
     __shared__ double sh[kReduceThreads];
     __shared__ double tot[12];
@@ -1577,30 +1581,43 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(DevBatch b, DevG
 #pragma unroll
         for (int i = 0; i < 12; ++i)
             q[i] = DF{0.f, 0.f};
+        if (parts & 1) {
 #pragma unroll 4
-        for (int k = threadIdx.x; k < I.n_nodes; k += blockDim.x) {
-            const int node = I.node_off + k;
-            float xk[3], Fk[3];
+            for (int k = threadIdx.x; k < I.n_nodes; k += blockDim.x) {
+                const int node = I.node_off + k;
+                float xk[3], Fk[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                xk[a] = x[a * N + node];
-                Fk[a] = F ? F[a * N + node] : 0.f;
-                df_add(q[a], xk[a]);
-                df_add(q[3 + a], Fk[a]);
-                df_add(q[9 + a], v ? v[a * N + node] : 0.f);
+                for (int a = 0; a < 3; ++a) {
+                    xk[a] = x[a * N + node];
+                    Fk[a] = F ? F[a * N + node] : 0.f;
+                    df_add(q[a], xk[a]);
+                    df_add(q[3 + a], Fk[a]);
+                }
+                df_add_prod(q[6], xk[1], Fk[2]);
+                df_add_prod(q[6], -xk[2], Fk[1]);
+                df_add_prod(q[7], xk[2], Fk[0]);
+                df_add_prod(q[7], -xk[0], Fk[2]);
+                df_add_prod(q[8], xk[0], Fk[1]);
+                df_add_prod(q[8], -xk[1], Fk[0]);
             }
-            df_add_prod(q[6], xk[1], Fk[2]);
-            df_add_prod(q[6], -xk[2], Fk[1]);
-            df_add_prod(q[7], xk[2], Fk[0]);
-            df_add_prod(q[7], -xk[0], Fk[2]);
-            df_add_prod(q[8], xk[0], Fk[1]);
-            df_add_prod(q[8], -xk[1], Fk[0]);
+        }
+        if ((parts & 2) && v) {
+#pragma unroll 4
+            for (int k = threadIdx.x; k < I.n_nodes; k += blockDim.x) {
+                const int node = I.node_off + k;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    df_add(q[9 + a], v[a * N + node]);
+            }
         }
 #pragma unroll
         for (int i = 0; i < 12; ++i)
             part[i][threadIdx.x] = make_float2(q[i].hi, q[i].lo);
         __syncthreads();
         for (int i = wid; i < 12; i += nw) {
+            const bool want = i < 9 ? (parts & 1) != 0 : (parts & 2) != 0;
+            if (!want)
+                continue;
             DF s{0.f, 0.f};
             for (int k = lane; k < (int)blockDim.x; k += 32) {
                 const float2 e = part[i][k];
@@ -1621,18 +1638,24 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(DevBatch b, DevG
             p[i] = 0.0;
         for (int k = threadIdx.x; k < I.n_nodes; k += blockDim.x) {
             const int node = I.node_off + k;
-            double xk[3], Fk[3];
+            if (parts & 1) {
+                double xk[3], Fk[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                xk[a] = (double)x[a * N + node];
-                Fk[a] = F ? (double)F[a * N + node] : 0.0;
-                p[a] += xk[a];
-                p[3 + a] += Fk[a];
-                p[9 + a] += v ? (double)v[a * N + node] : 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    xk[a] = (double)x[a * N + node];
+                    Fk[a] = F ? (double)F[a * N + node] : 0.0;
+                    p[a] += xk[a];
+                    p[3 + a] += Fk[a];
+                }
+                p[6] += xk[1] * Fk[2] - xk[2] * Fk[1];
+                p[7] += xk[2] * Fk[0] - xk[0] * Fk[2];
+                p[8] += xk[0] * Fk[1] - xk[1] * Fk[0];
             }
-            p[6] += xk[1] * Fk[2] - xk[2] * Fk[1];
-            p[7] += xk[2] * Fk[0] - xk[0] * Fk[2];
-            p[8] += xk[0] * Fk[1] - xk[1] * Fk[0];
+            if (parts & 2) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    p[9 + a] += v ? (double)v[a * N + node] : 0.0;
+            }
         }
 #pragma unroll
         for (int i = 0; i < 12; ++i) {
@@ -1654,20 +1677,24 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(DevBatch b, DevG
     __syncthreads();
     if (threadIdx.x == 0) {
         double *o = red + 12LL * blockIdx.x;
-        const double c[3] = {tot[0] / I.n_nodes, tot[1] / I.n_nodes, tot[2] / I.n_nodes};
-        const double *S = tot + 3;
-        o[0] = c[0];
-        o[1] = c[1];
-        o[2] = c[2];
-        o[3] = S[0];
-        o[4] = S[1];
-        o[5] = S[2];
-        o[6] = tot[6] - (c[1] * S[2] - c[2] * S[1]);
-        o[7] = tot[7] - (c[2] * S[0] - c[0] * S[2]);
-        o[8] = tot[8] - (c[0] * S[1] - c[1] * S[0]);
-        o[9] = tot[9];
-        o[10] = tot[10];
-        o[11] = tot[11];
+        if (parts & 1) {
+            const double c[3] = {tot[0] / I.n_nodes, tot[1] / I.n_nodes, tot[2] / I.n_nodes};
+            const double *S = tot + 3;
+            o[0] = c[0];
+            o[1] = c[1];
+            o[2] = c[2];
+            o[3] = S[0];
+            o[4] = S[1];
+            o[5] = S[2];
+            o[6] = tot[6] - (c[1] * S[2] - c[2] * S[1]);
+            o[7] = tot[7] - (c[2] * S[0] - c[0] * S[2]);
+            o[8] = tot[8] - (c[0] * S[1] - c[1] * S[0]);
+        }
+        if (parts & 2) {
+            o[9] = tot[9];
+            o[10] = tot[10];
+            o[11] = tot[11];
+        }
     }
 }
 
