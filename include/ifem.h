@@ -340,7 +340,10 @@ int ifem_volumes(ifem_ctx ctx, ifem_batch b, const void *x, double *vol, void *s
  *   A L^3 + B L^2 + C L + D = 0, A = 1/18 sum alpha.(alpha x alpha),
  *   B = 1/6 sum x.(alpha x alpha), C = 1/6 sum alpha.(x x x) (all cyclic over
  *   each face's nodes), D = V(x) - V0.
- * FP64 throughout (positions converted). V0: device double array of n_inst
+ * The cubic's sums and Lambda are FP64 in both precisions; with IFEM_FP32
+ * positions alpha comes from FP32 cross products of the ring's edge vectors
+ * (equal to the formula above on a closed ring), and since the cubic is built
+ * from that same alpha the corrected volume still meets V0. V0: device double array of n_inst
  * target volumes; lambda: device double array of n_inst receiving Lambda
  * (0 for solids, which are left unchanged), or NULL. An instance whose Newton
  * iteration does not converge in 100 steps is left unchanged and counted in

@@ -78,7 +78,8 @@ __global__ void __launch_bounds__(kVolThreads) volume_kernel(DevBatch b, const r
 
 // Thread per (instance, node) of a membrane: alpha_I = -(1/12) sum over the
 // incident faces, ascending, of x_{I2} x x_{I3} (the face's other two nodes
-// in cyclic order), in FP64. alpha: 3 doubles per node (batch node order).
+// in cyclic order); FP64 for FP64 positions, FP32 edge vectors for FP32
+// positions (below). alpha: 3 doubles per node (batch node order).
 template <typename real>
 __global__ void vc_alpha_kernel(DevBatch b, const real *__restrict__ x, double *__restrict__ alpha)
 {
@@ -88,22 +89,51 @@ __global__ void vc_alpha_kernel(DevBatch b, const real *__restrict__ x, double *
     if (T.kind != 0 || k >= T.n_nodes)
         return;
     const long long N = b.N;
-    double acc[3] = {0.0, 0.0, 0.0};
-    for (int q = T.inc_off[k]; q < T.inc_off[k + 1]; ++q) {
-        const int code = T.inc_idx[q], e = code >> 2, v = code & 3;
-        const int n1 = T.elems[3 * e + (v + 1) % 3], n2 = T.elems[3 * e + (v + 2) % 3];
-        double p1[3], p2[3], t[3];
-        load_node_d(x, N, I.node_off + n1, p1);
-        load_node_d(x, N, I.node_off + n2, p2);
-        cross3d(p1, p2, t);
+    double *o = alpha + 3 * (I.node_off + k);
+    if constexpr (std::is_same<real, float>::value) {
+        // FP32: over the closed ring sum x_I2 x x_I3 = sum (x_I2 - x_I) x (x_I3 - x_I)
+        // (the ring's edges x_I3 - x_I2 sum to zero), so the cross products
+        // take edge vectors about one cell long, exact enough in FP32; the
+        // correction's sums use this same alpha in FP64, so the corrected
+        // volume still meets V0
+        float pk[3], acc[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            acc[a] = acc[a] + t[a];
-    }
-    double *o = alpha + 3 * (I.node_off + k);
+            pk[a] = x[a * N + I.node_off + k];
+        for (int q = T.inc_off[k]; q < T.inc_off[k + 1]; ++q) {
+            const int code = T.inc_idx[q], e = code >> 2, v = code & 3;
+            const long long n1 = I.node_off + T.elems[3 * e + (v + 1) % 3];
+            const long long n2 = I.node_off + T.elems[3 * e + (v + 2) % 3];
+            float e1[3], e2[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-        o[a] = acc[a] * (-1.0 / 12.0);
+            for (int a = 0; a < 3; ++a) {
+                e1[a] = x[a * N + n1] - pk[a];
+                e2[a] = x[a * N + n2] - pk[a];
+            }
+            acc[0] += e1[1] * e2[2] - e1[2] * e2[1];
+            acc[1] += e1[2] * e2[0] - e1[0] * e2[2];
+            acc[2] += e1[0] * e2[1] - e1[1] * e2[0];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            o[a] = (double)acc[a] * (-1.0 / 12.0);
+    } else {
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int q = T.inc_off[k]; q < T.inc_off[k + 1]; ++q) {
+            const int code = T.inc_idx[q], e = code >> 2, v = code & 3;
+            const int n1 = T.elems[3 * e + (v + 1) % 3], n2 = T.elems[3 * e + (v + 2) % 3];
+            double p1[3], p2[3], t[3];
+            load_node_d(x, N, I.node_off + n1, p1);
+            load_node_d(x, N, I.node_off + n2, p2);
+            cross3d(p1, p2, t);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                acc[a] = acc[a] + t[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            o[a] = acc[a] * (-1.0 / 12.0);
+    }
 }
 
 // Block per instance of a membrane: the cubic A L^3 + B L^2 + C L + D = 0 of

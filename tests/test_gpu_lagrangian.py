@@ -128,7 +128,8 @@ def test_volume_correction(case, precision):
             assert lam[i] == 0.0 and np.array_equal(g[s], xp[s])
             continue
         xo, _, lo = O.volume_correction(tm.elems, xp[s], V0[i])
-        assert lam[i] == pytest.approx(lo, rel=1e-9)
+        # FP32: alpha from FP32 edge vectors, so Lambda carries their rounding
+        assert lam[i] == pytest.approx(lo, rel=1e-9 if precision == FP64 else 1e-5)
         scale = np.abs(xo).max()
         tol = 1e-12 if precision == FP64 else 2e-7
         np.testing.assert_allclose(g[s], xo, rtol=0, atol=tol * scale)
