@@ -236,7 +236,10 @@ def time_extras(wl, I, torch, dev, flush, T, reps=20, warm=3):
     """CUDA-event times of the Lagrangian-update and fluid-stress entry points
     on the resident workload (FP32, same context kind as the step), each with
     its algorithmic bytes: every node array read or written once, grid values
-    read (or read and written) once over the touched footprint."""
+    read (or read and written) once over the touched footprint. The coupling
+    step with the fused position update is timed beside the plain step, both
+    launched eagerly (no graph), so that their difference is the cost of the
+    update inside the step."""
     import math
     N = wl.n_nodes
     n_solid = int(sum(wl.templates[i.tmpl].n_nodes for i in wl.instances if wl.templates[i.tmpl].kind == "solid"))
@@ -261,7 +264,16 @@ def time_extras(wl, I, torch, dev, flush, T, reps=20, warm=3):
     I.ifem_volumes(cp.ctx, cp.batch, x0, vol, s)
     V0 = vol.clone()
     lam = torch.empty_like(vol)
+    u = cp.grid_to_device(wl.u)
+    vs, xn, f = cp.empty_nodes(), cp.empty_nodes(), cp.zeros_grid()
+    red = torch.zeros(12 * len(wl.instances) + 6 * len(wl.boxes), dtype=torch.float64, device=dev)
+    I.ifem_prepare(cp.ctx, cp.batch, x0, s)
+    step_bytes = 4 * 12 * N + 12 * T
     calls = {
+        "step_coupling": (lambda: I.ifem_step_coupling(cp.ctx, cp.batch, cp.grid, x0, u, F, f, vs, red, 0, s),
+                          step_bytes),
+        "step_coupling_ab2": (lambda: I.ifem_step_coupling_ab2(cp.ctx, cp.batch, cp.grid, x0, u, F, f, vs, red, 0,
+                                                               vp, 1e-4, xn, s), step_bytes + 24 * N),
         "interp_cc6": (lambda: I.ifem_interpolate_cc(cp.ctx, cp.batch, cp.grid, field, 6, x0, Cn, s),
                        12 * N + 24 * N + 6 * 4 * (T // 3)),
         "fluid_stress_forces": (lambda: I.ifem_fluid_stress_forces(cp.ctx, cp.batch, x0, v, Cn, 1.0, 0.5, 1.0, F,

@@ -176,7 +176,7 @@ const char *ifem_last_error(ifem_ctx ctx);
 int ifem_sync_status(ifem_ctx ctx, ifem_stats *out);
 /* Tile edge (cells) currently used by ctx (after autotuning, if any). */
 int ifem_ctx_tile(ifem_ctx ctx);
-/* Stage durations of the last ifem_step_coupling call on a context created
+/* Stage durations of the last ifem_step_coupling(_ab2) call on a context created
  * with cfg.profile = 1, measured with CUDA events recorded on that call's
  * stream: ms[0] binning, ms[1] forces, ms[2] spread, ms[3] interpolation,
  * ms[4] reductions (milliseconds); where the step fuses interpolation into
@@ -319,7 +319,8 @@ int ifem_indicator_source(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x
 /* Adams-Bashforth position update (Eq. Bashforth_eqn), in place:
  *   x = x + dt (3/2 v - 1/2 v_prev)
  * x, v, v_prev: device node arrays (x: the particles' local positions).
- * IFEM_FP64 evaluates x + dt*(1.5*v - 0.5*v_prev) in that order. For the
+ * Both precisions evaluate x + dt*(1.5*v - 0.5*v_prev) in that order, one
+ * rounding per operation (no fused multiply-adds). For the
  * first step pass v_prev = v (forward Euler). IFEM_ERR_ARG for a non-finite dt. */
 int ifem_ab2_update(ifem_ctx ctx, ifem_batch b, void *x, const void *v, const void *v_prev, double dt,
                     void *stream);
@@ -376,6 +377,24 @@ int ifem_reduce(ifem_ctx ctx, ifem_batch b, const void *x, const void *F, const 
  * those of the separate calls up to FP32 rounding. */
 int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *u,
                        void *F, void *f, void *v, double *red, int flags, void *stream);
+
+/* The coupling step followed by the position update of Algorithm step 4 and
+ * Eq. Bashforth_eqn, out of place:
+ *   x_new = x + dt (3/2 v - 1/2 v_prev)
+ * with v the velocities this step interpolates. Arguments as
+ * ifem_step_coupling, plus v_prev (device node array, the previous step's
+ * velocities; pass v_prev = a copy of v for a forward-Euler first step) and
+ * x_new (device node array receiving the new local positions). Where the
+ * step fuses the interpolation into the spreading kernel (IFEM_FP32,
+ * IFEM_SCATTER_ATOMIC, IFEM_KERNEL_PESKIN4) the same kernel also writes x_new
+ * from each velocity it gathers, so v is never read back; elsewhere the update
+ * runs after the interpolation on its stream. x_new equals ifem_ab2_update on
+ * a copy of x with the v this call writes (bit for bit). x_new may not overlap
+ * x, v, v_prev or F, nor v_prev overlap v (IFEM_ERR_ARG); IFEM_ERR_ARG for a
+ * non-finite dt. */
+int ifem_step_coupling_ab2(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *u,
+                           void *F, void *f, void *v, double *red, int flags, const void *v_prev,
+                           double dt, void *x_new, void *stream);
 
 /* Hessian-vector product of the elastic energy (bending excluded):
  *   Hw = d/de [-F_el(x + e w)] at e = 0,

@@ -777,8 +777,11 @@ static int do_spread(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
 
 // Spreading with the interpolation of the same step fused into it (the
 // halo-scatter configuration only): one launch per step for both transfers.
+// With xn given the launch also writes the position update from the
+// velocities it gathers (xn = x + dt (3/2 v - 1/2 vp)).
 static int do_spread_interp(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *F, const void *u,
-                            void *f, void *v, int flags, void *stream)
+                            void *f, void *v, int flags, void *stream, const void *vp = nullptr,
+                            void *xn = nullptr, double dt = 0.0)
 {
     if (flags & IFEM_SPREAD_OVERWRITE) {
         cudaError_t e = cudaMemsetAsync(f, 0, (size_t)g->total * real_size(ctx), (cudaStream_t)stream);
@@ -786,6 +789,9 @@ static int do_spread_interp(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void 
             return launch_rc(ctx, e, "spread overwrite");
     }
     TransferArgs a = transfer_args(ctx, b, x, F, u, f, v, flags, stream);
+    a.vp = vp;
+    a.xn = xn;
+    a.dt = dt;
     return launch_rc(ctx, launch_spread_f32(a), "spread + interpolate");
 }
 
@@ -794,6 +800,23 @@ static int do_interp(ifem_ctx ctx, ifem_batch b, const void *u, const void *x, v
     TransferArgs a = transfer_args(ctx, b, x, nullptr, u, nullptr, v, 0, stream);
     cudaError_t e = ctx->cfg.precision == IFEM_FP64 ? launch_interp_f64(a) : launch_interp_f32(a);
     return launch_rc(ctx, e, "interpolate");
+}
+
+// Out-of-place position update xn = x + dt (3/2 v - 1/2 vp) (Eq. Bashforth_eqn).
+static int do_ab2(ifem_ctx ctx, ifem_batch b, const void *x, const void *v, const void *vp, double dt, void *xn,
+                  void *stream)
+{
+    LagrangeArgs a{};
+    a.b = dev_batch(b);
+    a.x = const_cast<void *>(x);
+    a.x_out = xn;
+    a.v = v;
+    a.vp = vp;
+    a.dt = dt;
+    a.status = ctx->d_status;
+    a.stream = (cudaStream_t)stream;
+    cudaError_t e = ctx->cfg.precision == IFEM_FP64 ? launch_ab2_f64(a) : launch_ab2_f32(a);
+    return launch_rc(ctx, e, "position update");
 }
 
 static int do_reduce(ifem_ctx ctx, ifem_batch b, const void *x, const void *F, const void *v, double *red,
@@ -1004,19 +1027,16 @@ extern "C" int ifem_reduce(ifem_ctx ctx, ifem_batch b, const void *x, const void
     return do_reduce(ctx, b, x, F, v, red, stream);
 }
 
-extern "C" int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *u, void *F,
-                                  void *f, void *v, double *red, int flags, void *stream)
+// One coupling step; with xn given (the caller checked vp, dt and aliasing)
+// also the position update from the interpolated velocities.
+static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *u, void *F, void *f,
+                     void *v, double *red, int flags, const void *vp, double dt, void *xn, void *stream)
 {
-    int rc = check_call(ctx, b, g);
-    if (rc != IFEM_OK)
-        return rc;
-    if (!g || !u || !f || ((!x || !F || !v) && b->N > 0))
-        return fail(ctx, IFEM_ERR_ARG, "step_coupling: null array or grid");
-    if (flags & ~(IFEM_SPREAD_FORCE | IFEM_SPREAD_OVERWRITE))
-        return fail(ctx, IFEM_ERR_ARG, "step_coupling: unknown flags");
+    int rc;
     if (ctx->ev_ok) {
         // profiling: stages one after the other on the caller's stream, each
-        // bracketed by an event
+        // bracketed by an event (the position update counts with the
+        // interpolation)
         mark(ctx, 0, stream);
         if ((rc = do_bin(ctx, b, g, x, stream)) != IFEM_OK)
             return rc;
@@ -1026,7 +1046,7 @@ extern "C" int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const
         mark(ctx, 2, stream);
         ctx->ev_fused = use_halo(ctx);
         if (ctx->ev_fused) {
-            if ((rc = do_spread_interp(ctx, b, g, x, F, u, f, v, flags, stream)) != IFEM_OK)
+            if ((rc = do_spread_interp(ctx, b, g, x, F, u, f, v, flags, stream, vp, xn, dt)) != IFEM_OK)
                 return rc;
             mark(ctx, 3, stream);
         } else {
@@ -1034,6 +1054,8 @@ extern "C" int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const
                 return rc;
             mark(ctx, 3, stream);
             if ((rc = do_interp(ctx, b, u, x, v, stream)) != IFEM_OK)
+                return rc;
+            if (xn && (rc = do_ab2(ctx, b, x, v, vp, dt, xn, stream)) != IFEM_OK)
                 return rc;
         }
         mark(ctx, 4, stream);
@@ -1044,12 +1066,13 @@ extern "C" int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const
         return IFEM_OK;
     }
     // fork-join over the context's two auxiliary streams (also inside stream
-    // capture): forces run beside binning, interpolation beside spreading,
-    // and the x/F sums (which need only the forces) beside the transfers
+    // capture): forces run beside binning, interpolation (and the position
+    // update) beside spreading, and the x/F sums (which need only the forces)
+    // beside the transfers
     //   s:    bin ----------- wait(forces) spread  wait(interp) wait(sums) sums of v, boxes
     //   aux0: forces -------/ sums of x, F -----------------------/
-    //   aux1:       wait(bin) interp -------------/
-    // (with the fused spread + interpolation the aux1 branch is absent)
+    //   aux1:       wait(bin) interp [ab2] -------/
+    // (with the fused spread + interpolation [+ ab2] the aux1 branch is absent)
     const bool fused = use_halo(ctx) != 0;
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = ws_ensure(ctx, b, g, ctx->tile)) != IFEM_OK)
@@ -1079,13 +1102,15 @@ extern "C" int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const
             return launch_rc(ctx, e, "step_coupling fork");
         if ((rc = do_interp(ctx, b, u, x, v, ctx->aux[1])) != IFEM_OK)
             return rc;
+        if (xn && (rc = do_ab2(ctx, b, x, v, vp, dt, xn, ctx->aux[1])) != IFEM_OK)
+            return rc;
         if ((e = cudaEventRecord(ctx->fork[3], ctx->aux[1])) != cudaSuccess)
             return launch_rc(ctx, e, "step_coupling fork");
     }
     if ((e = cudaStreamWaitEvent(s, ctx->fork[1], 0)) != cudaSuccess)
         return launch_rc(ctx, e, "step_coupling join");
     if (fused) {
-        if ((rc = do_spread_interp(ctx, b, g, x, F, u, f, v, flags, stream)) != IFEM_OK)
+        if ((rc = do_spread_interp(ctx, b, g, x, F, u, f, v, flags, stream, vp, xn, dt)) != IFEM_OK)
             return rc;
     } else {
         if ((rc = do_spread(ctx, b, g, x, F, f, flags, stream)) != IFEM_OK)
@@ -1100,6 +1125,54 @@ extern "C" int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const
             return rc;
     }
     return IFEM_OK;
+}
+
+static int check_step(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *u, const void *F,
+                      const void *f, const void *v, int flags, const char *who)
+{
+    int rc = check_call(ctx, b, g);
+    if (rc != IFEM_OK)
+        return rc;
+    if (!g || !u || !f || ((!x || !F || !v) && b->N > 0))
+        return fail(ctx, IFEM_ERR_ARG, std::string(who) + ": null array or grid");
+    if (flags & ~(IFEM_SPREAD_FORCE | IFEM_SPREAD_OVERWRITE))
+        return fail(ctx, IFEM_ERR_ARG, std::string(who) + ": unknown flags");
+    return IFEM_OK;
+}
+
+extern "C" int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *u, void *F,
+                                  void *f, void *v, double *red, int flags, void *stream)
+{
+    int rc = check_step(ctx, b, g, x, u, F, f, v, flags, "step_coupling");
+    if (rc != IFEM_OK)
+        return rc;
+    return step_impl(ctx, b, g, x, u, F, f, v, red, flags, nullptr, 0.0, nullptr, stream);
+}
+
+extern "C" int ifem_step_coupling_ab2(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *u,
+                                      void *F, void *f, void *v, double *red, int flags, const void *v_prev,
+                                      double dt, void *x_new, void *stream)
+{
+    int rc = check_step(ctx, b, g, x, u, F, f, v, flags, "step_coupling_ab2");
+    if (rc != IFEM_OK)
+        return rc;
+    if ((!v_prev || !x_new) && b->N > 0)
+        return fail(ctx, IFEM_ERR_ARG, "step_coupling_ab2: null array");
+    if (!std::isfinite(dt))
+        return fail(ctx, IFEM_ERR_ARG, "step_coupling_ab2: dt must be finite");
+    if (b->N > 0) {
+        // x_new is written while x, v_prev and F are still read, and v_prev
+        // is read after v is written: none of them may overlap
+        const size_t nb = 3 * (size_t)b->N * real_size(ctx);
+        auto overlap = [nb](const void *p, const void *q) {
+            const char *a = (const char *)p, *c = (const char *)q;
+            return a < c + nb && c < a + nb;
+        };
+        if (overlap(x_new, x) || overlap(x_new, v) || overlap(x_new, v_prev) || overlap(x_new, F) ||
+            overlap(v_prev, v))
+            return fail(ctx, IFEM_ERR_ARG, "step_coupling_ab2: x_new, x, v, v_prev and F must not overlap");
+    }
+    return step_impl(ctx, b, g, x, u, F, f, v, red, flags, v_prev, dt, x_new, stream);
 }
 
 // Tile autotuner: time binning + spreading + interpolation of the batch at

@@ -148,6 +148,18 @@ __host__ __device__ inline int tiles_per_axis(int n, int t)
     return T;
 }
 
+// Adams-Bashforth position update of one value (Eq. Bashforth_eqn),
+// x + dt*(1.5*v - 0.5*vp) rounded operation by operation in this order (no
+// contraction into FMAs), so every kernel that takes it gives the same bits.
+__device__ __forceinline__ float ab2_value(float x, float v, float vp, float dt)
+{
+    return __fadd_rn(x, __fmul_rn(dt, __fsub_rn(__fmul_rn(1.5f, v), __fmul_rn(0.5f, vp))));
+}
+__device__ __forceinline__ double ab2_value(double x, double v, double vp, double dt)
+{
+    return __dadd_rn(x, __dmul_rn(dt, __dsub_rn(__dmul_rn(1.5, v), __dmul_rn(0.5, vp))));
+}
+
 // Reductions into shared memory addressed by 32-bit shared-window offsets
 // (no generic-to-shared address check per access).
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -317,6 +329,9 @@ struct TransferArgs {
     int n_sm;
     int acc64;        // FP32 spread: 64-bit (1) or 32-bit (0) fixed-point accumulators
     int halo;         // FP32 Peskin spread with halo scatter (IFEM_SCATTER_ATOMIC)
+    const void *vp;   // fused position update (halo spread + interpolation only):
+    void *xn;         //   xn = x + dt (3/2 v - 1/2 vp) when xn is not null
+    double dt;
     cudaStream_t stream;
 };
 
@@ -367,6 +382,7 @@ cudaError_t launch_interp_cc_f64(const TransferArgs &a, int ncomp);
 struct LagrangeArgs {
     DevBatch b;
     void *x;
+    void *x_out;      // AB2 result (null: in place)
     const void *v;
     const void *vp;
     double dt;

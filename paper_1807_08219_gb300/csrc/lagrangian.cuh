@@ -9,14 +9,15 @@
 
 namespace ifem {
 
-// x = x + dt*(1.5*v - 0.5*vp), componentwise over the 3N node values.
+// xo = x + dt*(1.5*v - 0.5*vp), componentwise over the 3N node values (in
+// place when xo == x).
 template <typename real>
-__global__ void ab2_kernel(long long n3, real *__restrict__ x, const real *__restrict__ v,
+__global__ void ab2_kernel(long long n3, const real *x, real *xo, const real *__restrict__ v,
                            const real *__restrict__ vp, real dt)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n3)
-        x[i] = x[i] + dt * (real(1.5) * v[i] - real(0.5) * vp[i]);
+        xo[i] = ab2_value(x[i], v[i], vp[i], dt);
 }
 
 __device__ __forceinline__ void cross3d(const double a[3], const double b[3], double r[3])

@@ -103,16 +103,19 @@ cudaError_t spread_impl(const TransferArgs &a)
         const int E = a.g.max_edge;
         cudaMemsetAsync(a.w.counters + 2, 0, sizeof(int), s);
         if (a.halo) {
-            // with u and v given, interpolation is fused into the spread
+            // with u and v given, interpolation is fused into the spread, and
+            // with xn also the position update
             const bool fused = a.u != nullptr && a.v != nullptr;
-            auto kern = fused ? spread_halo_kernel<true> : spread_halo_kernel<false>;
+            auto kern = !fused ? spread_halo_kernel<false>
+                               : (a.xn ? spread_halo_kernel<true, true> : spread_halo_kernel<true>);
             size_t sm = sizeof(int) * (size_t)halo_ints(E);
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             int occ = 1;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, sm);
             occ = occ < 1 ? 1 : occ;
             kern<<<a.n_sm * occ, 256, sm, s>>>(b, a.g, a.w, (const float *)a.x, (const float *)a.F, (float *)a.f,
-                                               a.density, (const float *)a.u, (float *)a.v);
+                                               a.density, (const float *)a.u, (float *)a.v,
+                                               (const float *)a.vp, (float *)a.xn, (float)a.dt);
             IFEM_LAUNCH_CHECK();
             return cudaSuccess;
         }
@@ -222,8 +225,9 @@ cudaError_t ab2_impl(const LagrangeArgs &a)
     const long long n3 = 3 * a.b.N;
     if (n3 == 0)
         return cudaSuccess;
-    ab2_kernel<real><<<(unsigned)((n3 + 255) / 256), 256, 0, a.stream>>>(n3, (real *)a.x, (const real *)a.v,
-                                                                         (const real *)a.vp, (real)a.dt);
+    ab2_kernel<real><<<(unsigned)((n3 + 255) / 256), 256, 0, a.stream>>>(
+        n3, (const real *)a.x, (real *)(a.x_out ? a.x_out : a.x), (const real *)a.v, (const real *)a.vp,
+        (real)a.dt);
     IFEM_LAUNCH_CHECK();
     return cudaSuccess;
 }

@@ -760,13 +760,18 @@ __host__ __device__ inline int halo_ints(int E)
 // INTERP = true fuses the interpolation S of the same step: each (node,
 // lattice) unit also gathers u at the 64 stencil points with the unscaled
 // weights it has just computed, v_d = sum phi u_d (Algorithm step 4).
-template <bool INTERP>
+// AB2 = true (with INTERP) also takes the position update of Eq.
+// Bashforth_eqn from the velocity it has just gathered, out of place:
+// xn_d = x_d + dt (3/2 v_d - 1/2 vp_d), rounded as in ab2_kernel.
+template <bool INTERP, bool AB2 = false>
 __global__ void __launch_bounds__(256, 5) spread_halo_kernel(DevBatch b, DevGrid g, DevWork w,
                                                           const float *__restrict__ x,
                                                           const float *__restrict__ F, float *__restrict__ f,
                                                           int density, const float *__restrict__ u,
-                                                          float *__restrict__ v)
+                                                          float *__restrict__ v, const float *__restrict__ vp,
+                                                          float *__restrict__ xn, float dt)
 {
+    static_assert(INTERP || !AB2, "the position update needs the fused interpolation");
     extern __shared__ __align__(16) unsigned char halo_smem[];
     int *acc = reinterpret_cast<int *>(halo_smem);
     const unsigned sacc = smem_u32(acc);
@@ -912,6 +917,10 @@ __global__ void __launch_bounds__(256, 5) spread_halo_kernel(DevBatch b, DevGrid
                     out += ph[2][c] * accz;
                 }
                 v[d * N + node] = out;
+                if constexpr (AB2) {
+                    const long long i = d * N + node;
+                    xn[i] = ab2_value(x[i], out, vp[i], dt);
+                }
             } else {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
