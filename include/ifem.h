@@ -176,7 +176,7 @@ const char *ifem_last_error(ifem_ctx ctx);
 int ifem_sync_status(ifem_ctx ctx, ifem_stats *out);
 /* Tile edge (cells) currently used by ctx (after autotuning, if any). */
 int ifem_ctx_tile(ifem_ctx ctx);
-/* Stage durations of the last ifem_step_coupling(_ab2) call on a context created
+/* Stage durations of the last ifem_step_coupling(_ab2, _host) call on a context created
  * with cfg.profile = 1, measured with CUDA events recorded on that call's
  * stream: ms[0] binning, ms[1] forces, ms[2] spread, ms[3] interpolation,
  * ms[4] reductions (milliseconds); where the step fuses interpolation into
@@ -395,6 +395,27 @@ int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, c
 int ifem_step_coupling_ab2(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *u,
                            void *F, void *f, void *v, double *red, int flags, const void *v_prev,
                            double dt, void *x_new, void *stream);
+
+/* The coupling step for a caller whose node arrays live in host memory (a
+ * fluid solver on the CPU, the paper's Algorithm steps 1, 2 and 4 with the
+ * exchange of x and v in the loop): x_host (3 x N, the context's real type,
+ * the layout of x) is copied into the device work array x, the step runs as
+ * ifem_step_coupling on x, u, F, f, v, red, and v is copied back into v_host
+ * (3 x N) and, when red_host is given, the sums into red_host (12*n_inst +
+ * 6*n_boxes doubles; needs red). All copies are asynchronous on `stream`
+ * and the context's auxiliary streams, joined back into `stream`: the host
+ * arrays must stay valid, and v_host and red_host are filled, only once
+ * `stream` has passed this point. Host arrays should be pinned
+ * (cudaHostAlloc); pageable memory works outside graph capture but copies
+ * without overlap. With IFEM_FP32, IFEM_SCATTER_ATOMIC and a batch of two or
+ * more particles the positions arrive in two halves (by particle) and each
+ * half's element forces start as soon as it has landed; v goes back beside
+ * the sums of v and the boxes. Results equal those of copying x in, calling
+ * ifem_step_coupling and copying v and red out. Returns IFEM_ERR_ARG for null
+ * host arrays (N > 0) or red_host without red. */
+int ifem_step_coupling_host(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x_host, void *x,
+                            const void *u, void *F, void *f, void *v, void *v_host, double *red,
+                            double *red_host, int flags, void *stream);
 
 /* Hessian-vector product of the elastic energy (bending excluded):
  *   Hw = d/de [-F_el(x + e w)] at e = 0,

@@ -113,7 +113,7 @@ extern "C" int ifem_ctx_create(const ifem_config *cfg, ifem_ctx *out)
             ifem_ctx_destroy(ctx);
             return IFEM_ERR_CUDA;
         }
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < ifem_ctx_s::kForkEvents; ++i)
         if (cudaEventCreateWithFlags(&ctx->fork[i], cudaEventDisableTiming) != cudaSuccess) {
             ifem_ctx_destroy(ctx);
             return IFEM_ERR_CUDA;
@@ -135,7 +135,7 @@ extern "C" int ifem_ctx_destroy(ifem_ctx ctx)
     for (int i = 0; i < 6; ++i)
         if (ctx->ev[i])
             cudaEventDestroy(ctx->ev[i]);
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < ifem_ctx_s::kForkEvents; ++i)
         if (ctx->fork[i])
             cudaEventDestroy(ctx->fork[i]);
     for (int i = 0; i < 2; ++i)
@@ -735,9 +735,14 @@ static TransferArgs transfer_args(ifem_ctx ctx, ifem_batch b, const void *x, con
     return a;
 }
 
-static int do_forces(ifem_ctx ctx, ifem_batch b, const void *x, void *F, const void *wv, int hvp, void *stream)
+// Forces of particles [inst0, inst0 + inst_n) only (inst_n = 0: all), where
+// forces_ranged_ok says the kernel takes a range.
+static int do_forces(ifem_ctx ctx, ifem_batch b, const void *x, void *F, const void *wv, int hvp, void *stream,
+                     int inst0 = 0, int inst_n = 0)
 {
     ForcesArgs a{};
+    a.inst0 = inst0;
+    a.inst_n = inst_n;
     a.b = dev_batch(b);
     a.w.elem_buf = b->d_elem_buf;
     a.w.bend_buf = b->d_bend_buf;
@@ -1027,16 +1032,52 @@ extern "C" int ifem_reduce(ifem_ctx ctx, ifem_batch b, const void *x, const void
     return do_reduce(ctx, b, x, F, v, red, stream);
 }
 
+// Host-resident node arrays of ifem_step_coupling_host: positions copied in
+// before the step, velocities and sums copied out after it.
+struct HostIO {
+    const void *x_host;
+    void *v_host;
+    double *red_host;
+    size_t red_n;   // doubles of red
+};
+
+// The FP32 one-CTA-per-particle force kernel takes a particle range, so the
+// forces of the particles whose positions have arrived can start while the
+// rest are still being copied in.
+static bool forces_ranged_ok(ifem_ctx ctx, ifem_batch b)
+{
+    return ctx->cfg.precision == IFEM_FP32 && ctx->cfg.scatter == IFEM_SCATTER_ATOMIC && b->fused_ok &&
+           b->inst.size() >= 2;
+}
+
+// Copy node rows [n0, n1) of the 3 x N host array into the device array.
+static cudaError_t copy_nodes_in(ifem_ctx ctx, ifem_batch b, const void *xh, void *x, long long n0, long long n1,
+                                 cudaStream_t s)
+{
+    const size_t rs = real_size(ctx), pitch = (size_t)b->N * rs;
+    if (n1 <= n0)
+        return cudaSuccess;
+    return cudaMemcpy2DAsync((char *)x + n0 * rs, pitch, (const char *)xh + n0 * rs, pitch, (size_t)(n1 - n0) * rs,
+                             3, cudaMemcpyHostToDevice, s);
+}
+
 // One coupling step; with xn given (the caller checked vp, dt and aliasing)
-// also the position update from the interpolated velocities.
+// also the position update from the interpolated velocities; with io given
+// the host copies in and out around it.
 static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *u, void *F, void *f,
-                     void *v, double *red, int flags, const void *vp, double dt, void *xn, void *stream)
+                     void *v, double *red, int flags, const void *vp, double dt, void *xn, void *stream,
+                     const HostIO *io = nullptr)
 {
     int rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    const size_t node_bytes = 3 * (size_t)b->N * real_size(ctx);
     if (ctx->ev_ok) {
         // profiling: stages one after the other on the caller's stream, each
         // bracketed by an event (the position update counts with the
-        // interpolation)
+        // interpolation; host copies lie outside the stages)
+        if (io && (e = copy_nodes_in(ctx, b, io->x_host, const_cast<void *>(x), 0, b->N, s)) != cudaSuccess)
+            return launch_rc(ctx, e, "step_coupling_host: copy in");
         mark(ctx, 0, stream);
         if ((rc = do_bin(ctx, b, g, x, stream)) != IFEM_OK)
             return rc;
@@ -1063,6 +1104,13 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
             return rc;
         mark(ctx, 5, stream);
         ctx->ev_recorded = 1;
+        if (io && node_bytes > 0 &&
+            (e = cudaMemcpyAsync(io->v_host, v, node_bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return launch_rc(ctx, e, "step_coupling_host: copy out");
+        if (io && io->red_host &&
+            (e = cudaMemcpyAsync(io->red_host, red, io->red_n * sizeof(double), cudaMemcpyDeviceToHost, s)) !=
+                cudaSuccess)
+            return launch_rc(ctx, e, "step_coupling_host: copy out");
         return IFEM_OK;
     }
     // fork-join over the context's two auxiliary streams (also inside stream
@@ -1072,18 +1120,49 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
     //   s:    bin ----------- wait(forces) spread  wait(interp) wait(sums) sums of v, boxes
     //   aux0: forces -------/ sums of x, F -----------------------/
     //   aux1:       wait(bin) interp [ab2] -------/
-    // (with the fused spread + interpolation [+ ab2] the aux1 branch is absent)
+    // (with the fused spread + interpolation [+ ab2] the aux1 branch is absent).
+    // With host arrays the positions arrive on s in two halves (by particle)
+    // when the force kernel takes particle ranges, each half's forces starting
+    // on aux0 once it has landed; v goes back to the host on aux1 beside the
+    // sums of v and the boxes:
+    //   s:    copy x[0:h] copy x[h:N] bin ... spread+interp  sums of v, boxes  copy red  wait(copy v)
+    //   aux0:   wait(x[0:h]) forces[0:h] wait(x[h:N]) forces[h:N] sums of x, F
+    //   aux1:                                           wait(v) copy v ------------------/
     const bool fused = use_halo(ctx) != 0;
-    cudaStream_t s = (cudaStream_t)stream;
     if ((rc = ws_ensure(ctx, b, g, ctx->tile)) != IFEM_OK)
         return rc;
-    cudaError_t e = cudaEventRecord(ctx->fork[0], s);
-    if (e == cudaSuccess)
-        e = cudaStreamWaitEvent(ctx->aux[0], ctx->fork[0], 0);
-    if (e != cudaSuccess)
-        return launch_rc(ctx, e, "step_coupling fork");
-    if ((rc = do_forces(ctx, b, x, F, nullptr, 0, ctx->aux[0])) != IFEM_OK)
-        return rc;
+    const bool split = io && forces_ranged_ok(ctx, b);
+    if (split) {
+        // halves by node count, cut at a particle boundary
+        const int ni = (int)b->inst.size();
+        int h = 1;
+        while (h < ni - 1 && b->h_inst[h].node_off < b->N / 2)
+            ++h;
+        const long long nh = b->h_inst[h].node_off;
+        if ((e = copy_nodes_in(ctx, b, io->x_host, const_cast<void *>(x), 0, nh, s)) == cudaSuccess &&
+            (e = cudaEventRecord(ctx->fork[5], s)) == cudaSuccess &&
+            (e = copy_nodes_in(ctx, b, io->x_host, const_cast<void *>(x), nh, b->N, s)) == cudaSuccess &&
+            (e = cudaEventRecord(ctx->fork[6], s)) == cudaSuccess)
+            e = cudaStreamWaitEvent(ctx->aux[0], ctx->fork[5], 0);
+        if (e != cudaSuccess)
+            return launch_rc(ctx, e, "step_coupling_host: copy in");
+        if ((rc = do_forces(ctx, b, x, F, nullptr, 0, ctx->aux[0], 0, h)) != IFEM_OK)
+            return rc;
+        if ((e = cudaStreamWaitEvent(ctx->aux[0], ctx->fork[6], 0)) != cudaSuccess)
+            return launch_rc(ctx, e, "step_coupling_host: copy in");
+        if ((rc = do_forces(ctx, b, x, F, nullptr, 0, ctx->aux[0], h, ni - h)) != IFEM_OK)
+            return rc;
+    } else {
+        if (io && (e = copy_nodes_in(ctx, b, io->x_host, const_cast<void *>(x), 0, b->N, s)) != cudaSuccess)
+            return launch_rc(ctx, e, "step_coupling_host: copy in");
+        e = cudaEventRecord(ctx->fork[0], s);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(ctx->aux[0], ctx->fork[0], 0);
+        if (e != cudaSuccess)
+            return launch_rc(ctx, e, "step_coupling fork");
+        if ((rc = do_forces(ctx, b, x, F, nullptr, 0, ctx->aux[0])) != IFEM_OK)
+            return rc;
+    }
     if ((e = cudaEventRecord(ctx->fork[1], ctx->aux[0])) != cudaSuccess)
         return launch_rc(ctx, e, "step_coupling fork");
     // the x/F sums need only the forces: they run on aux0 beside the transfers
@@ -1118,12 +1197,28 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
         if ((e = cudaStreamWaitEvent(s, ctx->fork[3], 0)) != cudaSuccess)
             return launch_rc(ctx, e, "step_coupling join");
     }
+    const bool v_out = io && node_bytes > 0;
+    if (v_out) {
+        // v is complete here: copy it back beside the remaining sums
+        if ((e = cudaEventRecord(ctx->fork[7], s)) == cudaSuccess &&
+            (e = cudaStreamWaitEvent(ctx->aux[1], ctx->fork[7], 0)) == cudaSuccess &&
+            (e = cudaMemcpyAsync(io->v_host, v, node_bytes, cudaMemcpyDeviceToHost, ctx->aux[1])) == cudaSuccess)
+            e = cudaEventRecord(ctx->fork[8], ctx->aux[1]);
+        if (e != cudaSuccess)
+            return launch_rc(ctx, e, "step_coupling_host: copy out");
+    }
     if (red) {
         if ((e = cudaStreamWaitEvent(s, ctx->fork[4], 0)) != cudaSuccess)
             return launch_rc(ctx, e, "step_coupling join");
         if ((rc = do_reduce(ctx, b, x, F, v, red, stream, 2)) != IFEM_OK)
             return rc;
     }
+    if (io && io->red_host &&
+        (e = cudaMemcpyAsync(io->red_host, red, io->red_n * sizeof(double), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess)
+        return launch_rc(ctx, e, "step_coupling_host: copy out");
+    if (v_out && (e = cudaStreamWaitEvent(s, ctx->fork[8], 0)) != cudaSuccess)
+        return launch_rc(ctx, e, "step_coupling_host: join");
     return IFEM_OK;
 }
 
@@ -1173,6 +1268,21 @@ extern "C" int ifem_step_coupling_ab2(ifem_ctx ctx, ifem_batch b, ifem_grid g, c
             return fail(ctx, IFEM_ERR_ARG, "step_coupling_ab2: x_new, x, v, v_prev and F must not overlap");
     }
     return step_impl(ctx, b, g, x, u, F, f, v, red, flags, v_prev, dt, x_new, stream);
+}
+
+extern "C" int ifem_step_coupling_host(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x_host, void *x,
+                                       const void *u, void *F, void *f, void *v, void *v_host, double *red,
+                                       double *red_host, int flags, void *stream)
+{
+    int rc = check_step(ctx, b, g, x, u, F, f, v, flags, "step_coupling_host");
+    if (rc != IFEM_OK)
+        return rc;
+    if ((!x_host || !v_host) && b->N > 0)
+        return fail(ctx, IFEM_ERR_ARG, "step_coupling_host: null host array");
+    if (red_host && !red)
+        return fail(ctx, IFEM_ERR_ARG, "step_coupling_host: red_host needs the device array red");
+    HostIO io{x_host, v_host, red_host, 12 * b->inst.size() + 6 * (size_t)g->n_boxes};
+    return step_impl(ctx, b, g, x, u, F, f, v, red, flags, nullptr, 0.0, nullptr, stream, &io);
 }
 
 // Tile autotuner: time binning + spreading + interpolation of the batch at

@@ -311,6 +311,8 @@ struct ForcesArgs {
     const void *wv;   // HVP direction (or null)
     int scatter;      // 0 det, 1 atomic
     int hvp;          // 1: compute Hw instead of F
+    int inst0, inst_n;  // particle range [inst0, inst0 + inst_n) (inst_n = 0: all); the FP32
+                        // one-CTA-per-particle kernel only (forces_ranged_ok)
     cudaStream_t stream;
 };
 

@@ -858,10 +858,10 @@ __device__ __forceinline__ void bend2_f32(const TmplDev &T, int k, const float *
 // Shared memory: 3n (x) + 3n (F) + n (kH) floats.
 static __global__ void __launch_bounds__(512, 2) forces_fused_f32_kernel(DevBatch b, const float *__restrict__ x,
                                                                       float *__restrict__ F,
-                                                                      unsigned long long *status)
+                                                                      unsigned long long *status, int inst0)
 {
     extern __shared__ float sm[];
-    const InstDev I = b.inst[blockIdx.x];
+    const InstDev I = b.inst[inst0 + blockIdx.x];   // particles inst0, inst0 + 1, ...
     const TmplDev T = b.tmpl[I.tmpl];
     const int nn = T.n_nodes;
     const long long N = b.N;

@@ -25,7 +25,8 @@ struct ifem_ctx_s {
     int acc64 = 0;
     int tuned = 0;
     cudaStream_t aux[2] = {};   // fork-join streams of ifem_step_coupling
-    cudaEvent_t fork[5] = {};
+    static constexpr int kForkEvents = 9;
+    cudaEvent_t fork[kForkEvents] = {};
 };
 
 struct ifem_tmpl_s {

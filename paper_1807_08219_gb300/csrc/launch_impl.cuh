@@ -29,12 +29,17 @@ cudaError_t forces_impl(const ForcesArgs &a)
     if constexpr (std::is_same<real, float>::value) {
         if (!a.hvp && a.scatter == 1 && b.fused_ok) {
         size_t sm = fused_smem_bytes(b.max_nodes);
+        const int n = a.inst_n > 0 ? a.inst_n : b.n_inst;
+        if (a.inst0 < 0 || a.inst0 + n > b.n_inst)
+            return cudaErrorInvalidValue;
         cudaFuncSetAttribute(forces_fused_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        forces_fused_f32_kernel<<<b.n_inst, 512, sm, s>>>(b, (const float *)a.x, (float *)a.F, a.w.status);
+        forces_fused_f32_kernel<<<n, 512, sm, s>>>(b, (const float *)a.x, (float *)a.F, a.w.status, a.inst0);
         IFEM_LAUNCH_CHECK();
         return cudaSuccess;
         }
     }
+    if (a.inst0 != 0 || (a.inst_n != 0 && a.inst_n != b.n_inst))
+        return cudaErrorInvalidValue;   // particle ranges: the one-CTA-per-particle kernel only
     dim3 blk(256);
     dim3 ge((b.max_elems + 255) / 256, b.n_inst);
     dim3 gn((b.max_nodes + 255) / 256, b.n_inst);

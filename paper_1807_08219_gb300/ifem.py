@@ -36,7 +36,7 @@ EXPORTS = (
     "ifem_grid_create", "ifem_grid_destroy", "ifem_grid_values", "ifem_grid_box_offset",
     "ifem_batch_create", "ifem_batch_destroy", "ifem_batch_nodes", "ifem_batch_instances",
     "ifem_batch_set_origins", "ifem_prepare", "ifem_compute_forces", "ifem_spread", "ifem_interpolate",
-    "ifem_reduce", "ifem_step_coupling", "ifem_step_coupling_ab2", "ifem_force_hvp", "ifem_compute_forces_noalloc",
+    "ifem_reduce", "ifem_step_coupling", "ifem_step_coupling_ab2", "ifem_step_coupling_host", "ifem_force_hvp", "ifem_compute_forces_noalloc",
     "ifem_interpolate_cc", "ifem_fluid_stress_forces", "ifem_ab2_update", "ifem_volumes", "ifem_volume_correct",
     "ifem_indicator_source",
 )
@@ -121,6 +121,7 @@ def load(build_if_missing: bool = True):
         "ifem_reduce": (i, [p, p, p, p, p, p, p]),
         "ifem_step_coupling": (i, [p, p, p, p, p, p, p, p, p, i, p]),
         "ifem_step_coupling_ab2": (i, [p, p, p, p, p, p, p, p, p, i, p, d, p, p]),
+        "ifem_step_coupling_host": (i, [p, p, p, p, p, p, p, p, p, p, p, p, i, p]),
         "ifem_force_hvp": (i, [p, p, p, p, p, p]),
         "ifem_compute_forces_noalloc": (i, [p, p, p, p, p]),
         "ifem_interpolate_cc": (i, [p, p, p, p, i, p, p, p]),
@@ -336,6 +337,17 @@ def ifem_step_coupling_ab2(ctx, b, g, x, u, F, f, v, red, flags: int, v_prev, dt
     return _check(ctx, load().ifem_step_coupling_ab2(ctx, b, g, _ptr(x), _ptr(u), _ptr(F), _ptr(f), _ptr(v),
                                                      _ptr(red), flags, _ptr(v_prev), float(dt), _ptr(x_new),
                                                      _stream(stream)))
+
+
+def ifem_step_coupling_host(ctx, b, g, x_host, x, u, F, f, v, v_host, red=None, red_host=None, flags: int = 0,
+                            stream=None):
+    """x_host, v_host, red_host: CPU tensors (pinned for overlap); the rest device tensors."""
+    for t in (x_host, v_host, red_host):
+        if t is not None and getattr(t, "is_cuda", False):
+            raise ValueError("ifem_step_coupling_host: x_host, v_host and red_host must be host tensors")
+    return _check(ctx, load().ifem_step_coupling_host(ctx, b, g, _ptr(x_host), _ptr(x), _ptr(u), _ptr(F), _ptr(f),
+                                                      _ptr(v), _ptr(v_host), _ptr(red), _ptr(red_host), flags,
+                                                      _stream(stream)))
 
 
 def ifem_force_hvp(ctx, b, x, w, Hw, stream=None):
