@@ -661,6 +661,9 @@ static int ws_ensure(ifem_ctx ctx, ifem_batch b, ifem_grid g, int tile)
     CK(alloc((void **)&w.own_cursor, sizeof(int) * (no + 1)));
     CK(alloc((void **)&w.own_nodes, sizeof(int) * (size_t)std::max<long long>(N, 1)));
     CK(alloc((void **)&w.own_rec, sizeof(float4) * (size_t)std::max<long long>(N, 1)));
+    w.wtab = nullptr;
+    if (ctx->cfg.precision == IFEM_FP64 && ctx->cfg.kernel == IFEM_KERNEL_PESKIN4)
+        CK(alloc((void **)&w.wtab, sizeof(DetW) * (size_t)std::max<long long>(N, 1)));
     CK(alloc((void **)&w.active, sizeof(int) * (nt + 1)));
     CK(alloc((void **)&w.counters, sizeof(int) * 8));
     CK(alloc((void **)&w.scan_blocks, sizeof(int) * 2 * (nb + 1)));
@@ -800,9 +803,13 @@ static int do_spread_interp(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void 
     return launch_rc(ctx, launch_spread_f32(a), "spread + interpolate");
 }
 
-static int do_interp(ifem_ctx ctx, ifem_batch b, const void *u, const void *x, void *v, void *stream)
+// use_wtab: the binning of this same x ran earlier on the stream (FP64 Peskin
+// stencils are read from its table instead of recomputed).
+static int do_interp(ifem_ctx ctx, ifem_batch b, const void *u, const void *x, void *v, void *stream,
+                     int use_wtab = 0)
 {
     TransferArgs a = transfer_args(ctx, b, x, nullptr, u, nullptr, v, 0, stream);
+    a.use_wtab = use_wtab;
     cudaError_t e = ctx->cfg.precision == IFEM_FP64 ? launch_interp_f64(a) : launch_interp_f32(a);
     return launch_rc(ctx, e, "interpolate");
 }
@@ -1094,7 +1101,7 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
             if ((rc = do_spread(ctx, b, g, x, F, f, flags, stream)) != IFEM_OK)
                 return rc;
             mark(ctx, 3, stream);
-            if ((rc = do_interp(ctx, b, u, x, v, stream)) != IFEM_OK)
+            if ((rc = do_interp(ctx, b, u, x, v, stream, 1)) != IFEM_OK)
                 return rc;
             if (xn && (rc = do_ab2(ctx, b, x, v, vp, dt, xn, stream)) != IFEM_OK)
                 return rc;
@@ -1179,7 +1186,7 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
             e = cudaStreamWaitEvent(ctx->aux[1], ctx->fork[2], 0);
         if (e != cudaSuccess)
             return launch_rc(ctx, e, "step_coupling fork");
-        if ((rc = do_interp(ctx, b, u, x, v, ctx->aux[1])) != IFEM_OK)
+        if ((rc = do_interp(ctx, b, u, x, v, ctx->aux[1], 1)) != IFEM_OK)
             return rc;
         if (xn && (rc = do_ab2(ctx, b, x, v, vp, dt, xn, ctx->aux[1])) != IFEM_OK)
             return rc;
@@ -1296,7 +1303,7 @@ static int autotune(ifem_ctx ctx, ifem_batch b, const void *x, void *stream)
 {
     ifem_grid g = b->grid0;
     const size_t rs = real_size(ctx);
-    const std::vector<int> cand = ctx->cfg.precision == IFEM_FP64 ? std::vector<int>{6, 8, 10}
+    const std::vector<int> cand = ctx->cfg.precision == IFEM_FP64 ? std::vector<int>{8, 12, 16}
                                                                    : std::vector<int>{8, 12, 16};
     void *F = nullptr, *v = nullptr, *u = nullptr, *f = nullptr;
     cudaStream_t s = (cudaStream_t)stream;

@@ -22,7 +22,8 @@ constexpr int kScanThreads = 512;  // tile-count scan: threads per block
 constexpr int kScanPer = 4;        // and values per thread
 constexpr int kScanBlock = kScanThreads * kScanPer;
 // FP32 fused force kernel: 7 floats of shared memory per template node
-constexpr int kFusedMaxSmemBytes = 227 * 1024;
+constexpr int kMaxCtaSmemBytes = 227 * 1024;   // opt-in dynamic shared memory of one CTA
+constexpr int kFusedMaxSmemBytes = kMaxCtaSmemBytes;
 __host__ __device__ inline size_t fused_smem_bytes(int n_nodes) { return (size_t)7 * n_nodes * sizeof(float); }
 constexpr int kStatusWords = 8;
 enum StatusWord {
@@ -98,6 +99,18 @@ struct DevGrid {
     const BoxDev *boxes;
 };
 
+// FP64 Peskin stencil of one node on the three MAC lattices (deterministic
+// FP64 path), computed once per binning from the positions: per lattice d
+// and axis a the wrapped first stencil index base[d][a] and the four weights
+// ph[d][a][m]; lo[a] is the wrapped cell index c - 2, the low corner of the
+// reach of all three lattices.
+struct DetW {
+    double ph[3][3][4];
+    int base[3][3];
+    int lo[3];
+};
+static_assert(sizeof(DetW) == 336, "DetW layout");
+
 struct DevWork {
     int *cand_count;    // n_tiles + 1
     int *cand_off;      // n_tiles + 1
@@ -116,6 +129,7 @@ struct DevWork {
     void *elem_buf;     // per element nodal forces (12 reals per element)
     void *bend_buf;     // per node bending scratch (A, kH, n[3], lap) 6 reals
     double *red_tile;   // per active tile: 3 FP64 sums of added spread values
+    DetW *wtab;         // N entries (FP64 Peskin only, else null): written by the binning
     unsigned long long *status;  // kStatusWords
 };
 
@@ -331,6 +345,7 @@ struct TransferArgs {
     int n_sm;
     int acc64;        // FP32 spread: 64-bit (1) or 32-bit (0) fixed-point accumulators
     int halo;         // FP32 Peskin spread with halo scatter (IFEM_SCATTER_ATOMIC)
+    int use_wtab;     // FP64 Peskin interpolation: read the stencils the binning of x tabulated
     const void *vp;   // fused position update (halo spread + interpolation only):
     void *xn;         //   xn = x + dt (3/2 v - 1/2 vp) when xn is not null
     double dt;

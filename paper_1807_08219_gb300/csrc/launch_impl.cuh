@@ -92,6 +92,12 @@ cudaError_t bin_impl(const TransferArgs &a, int det_sort, int with_cand)
         sort_segments_kernel<<<a.n_sm * 4, 512, 0, s>>>(w);
         IFEM_LAUNCH_CHECK();
     }
+    if constexpr (std::is_same<real, double>::value) {
+        if (a.kernel == 0 && w.wtab) {
+            det_weights_kernel<<<(unsigned)((3 * b.N + 255) / 256), 256, 0, s>>>(b, a.g, w.wtab, (const double *)a.x);
+            IFEM_LAUNCH_CHECK();
+        }
+    }
     return cudaSuccess;
 }
 
@@ -135,7 +141,27 @@ cudaError_t spread_impl(const TransferArgs &a)
         kern<<<a.n_sm * occ, 256, sm, s>>>(b, a.g, a.w, (const float *)a.x, (const float *)a.F, (float *)a.f,
                                            a.density, (float)a.support);
     } else {
-        auto kern = a.kernel == 0 ? spread_det_kernel<0> : spread_det_kernel<1>;
+        if (a.kernel == 0) {
+            // warp per (tile, lattice) over the binning's stencil table
+            if (!a.w.wtab)
+                return cudaErrorInvalidValue;
+            // as many warps per CTA (up to kDetWarps) as the largest tile's
+            // accumulators fit in one CTA's shared memory
+            const size_t per_warp = det_warp_bytes(a.g.max_edge);
+            const int warps = (int)std::min<size_t>(kDetWarps, kMaxCtaSmemBytes / per_warp);
+            if (warps < 1)
+                return cudaErrorInvalidValue;
+            const size_t sm = per_warp * warps;
+            cudaFuncSetAttribute(spread_det_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            int occ = 1;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, spread_det_warp_kernel, 32 * warps, sm);
+            occ = occ < 1 ? 1 : occ;
+            spread_det_warp_kernel<<<a.n_sm * occ, 32 * warps, sm, s>>>(b, a.g, a.w, (const double *)a.F,
+                                                                      (double *)a.f, a.density);
+            IFEM_LAUNCH_CHECK();
+            return cudaSuccess;
+        }
+        auto kern = spread_det_mls_kernel;
         int occ = 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kDetThreads, 0);
         occ = occ < 1 ? 1 : occ;
@@ -164,10 +190,12 @@ cudaError_t interp_impl(const TransferArgs &a)
         unsigned grid = (unsigned)((b.N + 255) / 256);
         if (a.kernel == 0)
             interp_kernel<real, true, 0><<<grid, 256, 0, a.stream>>>(b, a.g, a.w, (const real *)a.u,
-                                                                    (const real *)a.x, (real *)a.v, (real)a.support, 0);
+                                                                    (const real *)a.x, (real *)a.v, (real)a.support, 0,
+                                                                    a.use_wtab && a.w.wtab != nullptr);
         else
             interp_kernel<real, true, 1><<<grid, 256, 0, a.stream>>>(b, a.g, a.w, (const real *)a.u,
-                                                                    (const real *)a.x, (real *)a.v, (real)a.support, 0);
+                                                                    (const real *)a.x, (real *)a.v, (real)a.support, 0,
+                                                                    0);
     }
     IFEM_LAUNCH_CHECK();
     return cudaSuccess;

@@ -359,6 +359,50 @@ __device__ __forceinline__ long long peskin_axis(real s, real ph[4])
     return i0;
 }
 
+// FP64 Peskin stencils of every node on the three lattices (thread per
+// (node, lattice)), computed once after binning: the deterministic spread
+// stages its candidates from this table instead of re-evaluating them for
+// every tile a node reaches, and the step's interpolation reads it too. The
+// values are those of peskin_axis<double> on the same coordinates (same
+// expressions, same compilation), bit for bit. Non-finite nodes are never
+// binned and their entries are left unwritten.
+static __global__ void det_weights_kernel(DevBatch b, DevGrid g, DetW *__restrict__ wt, const double *__restrict__ x)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long N = b.N;
+    if (t >= 3 * N)
+        return;
+    const long long node = t / 3;
+    const int d = (int)(t - 3 * node);
+    const InstDev I = b.inst[b.node_inst[node]];
+    const BoxDev B = g.boxes[I.box];
+    double xl[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        xl[a] = x[a * N + node];
+    if (!(isfinite(xl[0]) && isfinite(xl[1]) && isfinite(xl[2])))
+        return;
+    DetW &W = wt[node];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int I0;
+        const double sa = LatCoord<double>::get(I, B, a, xl[a], (double)mac_off(d, a), I0);
+        double ph[4];
+        W.base[d][a] = wrapi(peskin_axis<double>(sa, ph), B.n);
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            W.ph[d][a][m] = ph[m];
+    }
+    if (d == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int I0;
+            const double sc = LatCoord<double>::get(I, B, a, xl[a], 0.0, I0);
+            W.lo[a] = wrapi((long long)floor(sc) - 2, B.n);
+        }
+    }
+}
+
 // Per-thread partial sums as unevaluated float pairs (hi + lo, Knuth's
 // TwoSum and the FMA product error): about 44 significant bits, at FP32
 // speed; the FP64 pipe of this GPU is far narrower than its FP32 pipe.
@@ -1100,43 +1144,32 @@ __global__ void __launch_bounds__(256, 6) interp_direct_kernel(DevBatch b, DevGr
     v[d * N + node] = out;
 }
 
-// ---------------------------------------------- spread, FP64 deterministic
+// ---------------------------------------- spread, FP64 deterministic, MLS
 // Owner-computes gather: each thread owns up to kDetCells values of the tile
 // (per lattice), starts from the current grid value and adds the
 // contributions of the tile's candidate nodes in ascending node order:
-// f = f + w*g, w = (phi_x*phi_y)*phi_z, g = F*scale. This is the oracle's
-// per-value summation order, so the result is bit-identical.
+// f = f + w*g with the node's MLS weight w of that value, g = F*scale. This is
+// the oracle's per-value summation order, so the result is bit-identical.
+// (The Peskin kernel has its own warp-per-unit kernel, spread_det_warp_kernel.)
 constexpr int kDetThreads = 256;
 constexpr int kDetCells = 4;     // owned values per thread and lattice (1024 per chunk; 2 CTAs per SM)
 constexpr int kDetChunk = 32;    // candidates staged per round
 
-template <int KER>
-struct DetCand;
-template <>
-struct DetCand<0> {
+struct DetCand {
     int lo[3];            // wrapped cell c-2 (union reach of all lattices)
-    int base[3][3];       // [d][a] wrapped i0
-    double ph[3][3][4];   // [d][a][m]
-    double g[3];
-    int ok;
-};
-template <>
-struct DetCand<1> {
-    int lo[3];
-    int base[3][3];
-    double wt[3][27];
+    int base[3][3];       // [d][a] wrapped first stencil index
+    double wt[3][27];     // [d][J] MLS weights
     double g[3];
     int ok;
 };
 
-template <int KER>
-__global__ void __launch_bounds__(kDetThreads, 2) spread_det_kernel(DevBatch b, DevGrid g, DevWork w,
+static __global__ void __launch_bounds__(kDetThreads, 2) spread_det_mls_kernel(DevBatch b, DevGrid g, DevWork w,
                                                                  const double *__restrict__ x,
                                                                  const double *__restrict__ F,
                                                                  double *__restrict__ f, int density,
                                                                  double support)
 {
-    __shared__ DetCand<KER> cand[kDetChunk];
+    __shared__ DetCand cand[kDetChunk];
     __shared__ double red_sh[3][kDetThreads / 32];
     const long long N = b.N;
     const int n_active = w.counters[0];
@@ -1182,8 +1215,8 @@ __global__ void __launch_bounds__(kDetThreads, 2) spread_det_kernel(DevBatch b, 
                 for (int t = threadIdx.x; t < nc * 3; t += blockDim.x) {
                     const int j = t / 3, d = t % 3;
                     const int node = w.cand_nodes[c0 + j];
+                    DetCand &C = cand[j];
                     const InstDev I = b.inst[b.node_inst[node]];
-                    DetCand<KER> &C = cand[j];
                     double s[3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
@@ -1200,27 +1233,21 @@ __global__ void __launch_bounds__(kDetThreads, 2) spread_det_kernel(DevBatch b, 
                         }
                     }
                     C.g[d] = F[d * N + node] * scale;
-                    if constexpr (KER == 0) {
+                    int base[3];
+                    if (!mls_weights<double>(s, support, base, C.wt[d])) {
+                        status_add(w.status, ST_DOMAIN, 1);
+                        C.g[d] = 0.0;
 #pragma unroll
-                        for (int a = 0; a < 3; ++a)
-                            C.base[d][a] = wrapi(peskin_axis<double>(s[a], C.ph[d][a]), B.n);
-                    } else {
-                        int base[3];
-                        if (!mls_weights<double>(s, support, base, C.wt[d])) {
-                            status_add(w.status, ST_DOMAIN, 1);
-                            C.g[d] = 0.0;
-#pragma unroll
-                            for (int J = 0; J < 27; ++J)
-                                C.wt[d][J] = 0.0;
-                        }
-#pragma unroll
-                        for (int a = 0; a < 3; ++a)
-                            C.base[d][a] = wrapi(base[a], B.n);
+                        for (int J = 0; J < 27; ++J)
+                            C.wt[d][J] = 0.0;
                     }
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        C.base[d][a] = wrapi(base[a], B.n);
                 }
                 __syncthreads();
                 for (int j = 0; j < nc; ++j) {
-                    const DetCand<KER> &C = cand[j];
+                    const DetCand &C = cand[j];
 #pragma unroll
                     for (int q = 0; q < kDetCells; ++q) {
                         if (cbase + threadIdx.x + q * kDetThreads >= vol)
@@ -1237,15 +1264,8 @@ __global__ void __launch_bounds__(kDetThreads, 2) spread_det_kernel(DevBatch b, 
                             mx += mx < 0 ? B.n : 0;
                             my += my < 0 ? B.n : 0;
                             mz += mz < 0 ? B.n : 0;
-                            if constexpr (KER == 0) {
-                                if (mx <= 3 && my <= 3 && mz <= 3) {
-                                    double wgt = (C.ph[d][0][mx] * C.ph[d][1][my]) * C.ph[d][2][mz];
-                                    accv[q][d] = accv[q][d] + wgt * C.g[d];
-                                }
-                            } else {
-                                if (mx <= 2 && my <= 2 && mz <= 2)
-                                    accv[q][d] = accv[q][d] + C.wt[d][(mz * 3 + my) * 3 + mx] * C.g[d];
-                            }
+                            if (mx <= 2 && my <= 2 && mz <= 2)
+                                accv[q][d] = accv[q][d] + C.wt[d][(mz * 3 + my) * 3 + mx] * C.g[d];
                         }
                     }
                 }
@@ -1283,6 +1303,122 @@ __global__ void __launch_bounds__(kDetThreads, 2) spread_det_kernel(DevBatch b, 
     }
 }
 
+// FP64 deterministic Peskin spread, one warp per (tile, lattice) unit. The
+// unit's owned values sit in a shared-memory accumulator loaded from f; the
+// warp walks the tile's candidates in ascending node order, spreading each
+// candidate's 64 stencil points over its lanes (two points per lane, on
+// distinct cells since every box has at least 8 cells per axis), with a warp
+// barrier between candidates, so every value receives its terms in the
+// oracle's node order, f = f + ((phi_x phi_y) phi_z) g. Every lane carries
+// FP64 work on every candidate whose stencil it meets inside the tile (this
+// GPU's FP64 pipe is charged per warp instruction, whatever the active
+// lanes). Stencils come from the binning's table (det_weights_kernel).
+constexpr int kDetWarps = 4;   // units (warps) per CTA at most
+constexpr int kDetStage = 32;  // candidates staged per round
+struct DetStage {
+    double ph[3][4];
+    double g;
+    int base[3];
+    int pad;
+};
+// Shared memory of one warp: the accumulator of the largest tile + staging.
+__host__ __device__ inline size_t det_warp_bytes(int max_edge)
+{
+    const size_t e3 = (size_t)max_edge * max_edge * max_edge;
+    return e3 * sizeof(double) + kDetStage * sizeof(DetStage);
+}
+
+static __global__ void __launch_bounds__(32 * kDetWarps) spread_det_warp_kernel(DevBatch b, DevGrid g, DevWork w,
+                                                                              const double *__restrict__ F,
+                                                                              double *__restrict__ f, int density)
+{
+    extern __shared__ __align__(16) unsigned char det_smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const size_t e3 = (size_t)g.max_edge * g.max_edge * g.max_edge;
+    double *acc = reinterpret_cast<double *>(det_smem) + wid * e3;
+    DetStage *st = reinterpret_cast<DetStage *>(reinterpret_cast<double *>(det_smem) + nw * e3) + wid * kDetStage;
+    const long long N = b.N;
+    const int n_active = w.counters[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        status_add(w.status, ST_PAIRS, (unsigned long long)w.cand_off[g.n_tiles]);
+        status_add(w.status, ST_ACTIVE, (unsigned long long)n_active);
+    }
+    // this lane's stencil points: (a, bb, c0) and (a, bb, c0 + 2)
+    const int a = lane & 3, bb = (lane >> 2) & 3, c0 = lane >> 4;
+    const long long n_units = 3LL * n_active;
+    for (long long unit = (long long)blockIdx.x * nw + wid; unit < n_units; unit += (long long)gridDim.x * nw) {
+        const int tile = w.active[unit / 3];
+        const int d = (int)(unit - 3 * (unit / 3));
+        const TileInfo ti = decode_tile(g, tile);
+        const BoxDev B = g.boxes[ti.box];
+        const int ex = ti.edge[0], ey = ti.edge[1], ez = ti.edge[2];
+        const int sx = ti.start[0], sy = ti.start[1], sz = ti.start[2];
+        const int n = B.n, vol = ex * ey * ez;
+        double *fd = f + B.grid_off + (long long)d * n * n * n;
+        for (int i = lane; i < vol; i += 32) {
+            const int lx = i % ex, ly = (i / ex) % ey, lz = i / (ex * ey);
+            acc[i] = fd[((long long)(sz + lz) * n + sy + ly) * n + sx + lx];
+        }
+        const double scale = density ? B.scale : 1.0;
+        const int beg = w.cand_off[tile], end = w.cand_off[tile + 1];
+        for (int c = beg; c < end; c += kDetStage) {
+            const int nc = min(kDetStage, end - c);
+            __syncwarp();
+            if (lane < nc) {
+                const int node = w.cand_nodes[c + lane];
+                const DetW &Wn = w.wtab[node];
+                DetStage &S = st[lane];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    S.base[q] = Wn.base[d][q];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        S.ph[q][m] = Wn.ph[d][q][m];
+                }
+                S.g = F[d * N + node] * scale;
+            }
+            __syncwarp();
+            for (int j = 0; j < nc; ++j) {
+                const DetStage &S = st[j];
+                // tile-relative cell of each point (base is wrapped into [0, n))
+                int lx = S.base[0] + a - sx, ly = S.base[1] + bb - sy;
+                int lz0 = S.base[2] + c0 - sz, lz1 = lz0 + 2;
+                lx += lx < 0 ? n : (lx >= n ? -n : 0);
+                ly += ly < 0 ? n : (ly >= n ? -n : 0);
+                lz0 += lz0 < 0 ? n : (lz0 >= n ? -n : 0);
+                lz1 += lz1 < 0 ? n : (lz1 >= n ? -n : 0);
+                if ((unsigned)lx < (unsigned)ex && (unsigned)ly < (unsigned)ey) {
+                    const double t = S.ph[0][a] * S.ph[1][bb];
+                    if ((unsigned)lz0 < (unsigned)ez) {
+                        const int i = (lz0 * ey + ly) * ex + lx;
+                        acc[i] = acc[i] + (t * S.ph[2][c0]) * S.g;
+                    }
+                    if ((unsigned)lz1 < (unsigned)ez) {
+                        const int i = (lz1 * ey + ly) * ex + lx;
+                        acc[i] = acc[i] + (t * S.ph[2][c0 + 2]) * S.g;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        // write back; the unit's FP64 sum of the values it added
+        double part = 0.0;
+        for (int i = lane; i < vol; i += 32) {
+            const int lx = i % ex, ly = (i / ex) % ey, lz = i / (ex * ey);
+            double *p = fd + ((long long)(sz + lz) * n + sy + ly) * n + sx + lx;
+            const double old = *p;
+            *p = acc[i];
+            part += acc[i] - old;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            part += __shfl_down_sync(0xffffffffu, part, o);
+        if (lane == 0)
+            w.red_tile[3LL * tile + d] = part * (1.0 / B.scale);
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------- interp
 // Thread per node (in tile order for locality). DET: the oracle's order,
 // acc = acc + ((phi_x*phi_y)*phi_z)*u from 0, z-outer, x-inner. Fast FP32:
@@ -1290,7 +1426,8 @@ __global__ void __launch_bounds__(kDetThreads, 2) spread_det_kernel(DevBatch b, 
 template <typename real, bool DET, int KER>
 __global__ void __launch_bounds__(256) interp_kernel(DevBatch b, DevGrid g, DevWork w,
                                                      const real *__restrict__ u, const real *__restrict__ x,
-                                                     real *__restrict__ v, real support, int use_order)
+                                                     real *__restrict__ v, real support, int use_order,
+                                                     int use_wtab)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     // in tile order only the binned nodes are listed (non-finite ones are not)
@@ -1324,14 +1461,27 @@ __global__ void __launch_bounds__(256) interp_kernel(DevBatch b, DevGrid g, DevW
         if constexpr (KER == 0) {
             real ph[3][4];
             int ix[4], iy[4], iz[4];
+            // with use_wtab the stencil comes from the binning's per-node table
+            // (det_weights_kernel: the same values, computed once per node)
+            const DetW *wt = nullptr;
+            if constexpr (std::is_same<real, double>::value)
+                wt = use_wtab ? &w.wtab[node] : nullptr;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                int I0;
-                real s = LatCoord<real>::get(I, B, a, xl[a], (real)mac_off(d, a), I0);
-                long long i0 = peskin_axis<real>(s, ph[a]);
+                long long i0;
+                if (wt) {
+                    i0 = wt->base[d][a];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        ph[a][m] = (real)wt->ph[d][a][m];
+                } else {
+                    int I0;
+                    real s = LatCoord<real>::get(I, B, a, xl[a], (real)mac_off(d, a), I0);
+                    i0 = I0 + peskin_axis<real>(s, ph[a]);
+                }
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
-                    int wi = wrapi(I0 + i0 + m, n);
+                    int wi = wrapi(i0 + m, n);
                     if (a == 0) ix[m] = wi;
                     else if (a == 1) iy[m] = wi;
                     else iz[m] = wi;
