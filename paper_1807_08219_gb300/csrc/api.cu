@@ -1303,7 +1303,7 @@ static int autotune(ifem_ctx ctx, ifem_batch b, const void *x, void *stream)
 {
     ifem_grid g = b->grid0;
     const size_t rs = real_size(ctx);
-    const std::vector<int> cand = ctx->cfg.precision == IFEM_FP64 ? std::vector<int>{8, 12, 16}
+    const std::vector<int> cand = ctx->cfg.precision == IFEM_FP64 ? std::vector<int>{6, 8, 10, 12}
                                                                    : std::vector<int>{8, 12, 16};
     void *F = nullptr, *v = nullptr, *u = nullptr, *f = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
