@@ -44,10 +44,10 @@ REF_BUDGET_S = 150.0   # --impl reference: warm-up + timed oracle steps
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the current kernels on the C4 suspension (profiles/*_c4_fp32.md),
 # reported for that workload only; set an entry to None when its kernel changes.
-NCU_TRAFFIC = {"spread+interp": 462.2e6, "spread": None, "interp": None, "forces": None, "bin": None}
+NCU_TRAFFIC = {"spread+interp": 461.7e6, "spread": None, "interp": None, "forces": None, "bin": None}
 # The unit that bounds each kernel in that capture and its fraction of peak (context for the HBM
 # fraction: the fused transfer kernel is limited by the L1 load/store pipe, not by DRAM).
-NCU_LIMITER = {"spread+interp": ("l1tex load/store data-pipe wavefronts", 0.841),
+NCU_LIMITER = {"spread+interp": ("l1tex load/store data-pipe wavefronts", 0.845),
                "forces": ("shared-memory wavefronts", 0.598)}
 
 

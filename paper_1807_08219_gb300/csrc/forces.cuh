@@ -555,13 +555,19 @@ __device__ __forceinline__ void tri_geom(const real p[3][3], TriGeom<real> &t)
 // Pass 1 at vertex i (template-local id k), over its incident triangles in
 // ascending order: K += cot_k (x_i - x_j) + cot_j (x_i - x_k); mixed Voronoi
 // area (Voronoi region if no corner is obtuse, area/2 at an obtuse corner,
-// area/4 at the others); corner-angle sum; area-weighted normal. Outputs A,
+// area/4 at the others); corner angles; area-weighted normal. Outputs A,
 // kH = K.n/2 (K /= 2A), kG = (2 pi - angles)/A and the unit normal n.
+// The cotangents share one reciprocal of 2A per triangle. The angle deficit
+// 2 pi - sum theta is minus the argument of prod (dot + i 2A) over the corners
+// (each factor has argument theta), one atan2 per vertex instead of one per
+// corner; it equals the angle sum's deficit while that lies in (-pi, pi), and
+// the product is rescaled by an exact power of two if it grows small.
 template <typename real, typename Load>
 __device__ inline void bend_vertex_pass1(const TmplDev &T, int k, Load ld, real &A_out, real &kH_out,
                                          real &kG_out, real n_out[3])
 {
-    real K[3] = {0, 0, 0}, nrm[3] = {0, 0, 0}, A = 0, ang = 0;
+    real K[3] = {0, 0, 0}, nrm[3] = {0, 0, 0}, A = 0;
+    real zr = 1, zi = 0;   // running product of (dot + i 2A) over the corners
     for (int q = T.inc_off[k]; q < T.inc_off[k + 1]; ++q) {
         // incident triangle rotated to start at this vertex: (k, j, l)
         const int2 jk = T.ring[q];
@@ -572,7 +578,8 @@ __device__ inline void bend_vertex_pass1(const TmplDev &T, int k, Load ld, real 
         ld(jk.y, p[2]);
         TriGeom<real> t;
         tri_geom(p, t);
-        real cj = t.dot[c1] / t.twoA, ck = t.dot[c2] / t.twoA;
+        const real inv2A = real(1) / t.twoA;
+        real cj = t.dot[c1] * inv2A, ck = t.dot[c2] * inv2A;
         real eij[3], eik[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -592,7 +599,13 @@ __device__ inline void bend_vertex_pass1(const TmplDev &T, int k, Load ld, real 
         else
             Ai = t.twoA / real(8);
         A += Ai;
-        ang += atan2(t.twoA, t.dot[c]);
+        const real pr = zr * t.dot[c] - zi * t.twoA, pi = zr * t.twoA + zi * t.dot[c];
+        zr = pr;
+        zi = pi;
+        if (fabs(zr) + fabs(zi) < real(1e-30)) {
+            zr *= real(1099511627776.0);   // 2^40, exact
+            zi *= real(1099511627776.0);
+        }
 #pragma unroll
         for (int a = 0; a < 3; ++a)
             nrm[a] += t.fn[a];
@@ -605,7 +618,7 @@ __device__ inline void bend_vertex_pass1(const TmplDev &T, int k, Load ld, real 
     }
     A_out = A;
     kH_out = real(0.5) * (K[0] * n_out[0] + K[1] * n_out[1] + K[2] * n_out[2]);
-    kG_out = (real(6.283185307179586) - ang) / A;
+    kG_out = -atan2(zi, zr) / A;
 }
 
 // Pass 2 at vertex k: cotangent Laplacian of (kH - kH0) and the force.
@@ -623,8 +636,9 @@ __device__ inline void bend_vertex_pass2(const TmplDev &T, int k, Load ld, LoadH
         ld(jk.y, p[2]);
         TriGeom<real> t;
         tri_geom(p, t);
-        lap += (t.dot[2] / t.twoA) * ((kHof(jk.x) - kH0) - (kH - kH0))
-             + (t.dot[1] / t.twoA) * ((kHof(jk.y) - kH0) - (kH - kH0));
+        const real inv2A = real(1) / t.twoA;
+        lap += (t.dot[2] * inv2A) * ((kHof(jk.x) - kH0) - (kH - kH0))
+             + (t.dot[1] * inv2A) * ((kHof(jk.y) - kH0) - (kH - kH0));
     }
     real L = lap / (real(2) * A);
     real dh = kH - kH0;
