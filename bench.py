@@ -68,17 +68,18 @@ class Clocks:
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
 
-    def __init__(self, gpu: int):
+    def __init__(self, gpu: int, interval_ms: int = 20):
         self.gpu = gpu
+        self.interval_ms = interval_ms
         self.proc = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(self.interval_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
 
@@ -91,7 +92,7 @@ class Clocks:
         except Exception:
             self.proc.kill()
             out = ""
-        sm, smax, reasons = [], [], set()
+        sm, smax, busy, reasons = [], [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         for line in out.strip().splitlines():
             f = [s.strip() for s in line.split(",")]
@@ -102,11 +103,18 @@ class Clocks:
                 smax.append(float(f[2]))
             except ValueError:
                 continue
+            try:
+                if float(f[9]) >= 50.0:
+                    busy.append(sm[-1])
+            except (IndexError, ValueError):
+                pass
             for n, val in zip(names, f[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(busy or sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "samples_busy": len(busy),
+                "interval_ms": self.interval_ms,
+                "window": "every timed GPU loop of the run (headline steps, stage times, end-to-end, extras, FP64)"}
 
 
 def algorithmic_bytes(N, T, P, real=4):
@@ -123,11 +131,22 @@ def algorithmic_bytes(N, T, P, real=4):
         "forces": 2 * 3 * real * N,                     # x read, F written
         "spread": 2 * 3 * real * N + 4 * lists + 2 * real * T,  # x, F read; node list read; f read + written
         "interp": 2 * 3 * real * N + 4 * N + real * T,  # x read, v written, order list read; u read
-        # spread with the interpolation fused: x, F read, v written, node list read; f read + written, u read
-        "spread+interp": 3 * 3 * real * N + 4 * lists + 3 * real * T,
+        # spread with the interpolation fused: x, F read, v written; f read + written, u read
+        "spread+interp": 3 * 3 * real * N + 3 * real * T,
         "reduce": 3 * 3 * real * N,                     # x, F, v read
-        "step": 4 * 3 * real * N + 3 * real * T,        # x, v, F write + read; u read, f read + written
+        # the coupling step as one operation: x read, v written; u read, f read + written
+        "step": 2 * 3 * real * N + 3 * real * T,
+        # the same with the nodal forces F written and read back (the step's F output)
+        "step_with_F": 4 * 3 * real * N + 3 * real * T,
     }
+
+
+def flush_l2(flush, stream):
+    """Write a buffer larger than L2 (129 MB) on the timed stream, so that the
+    next timed work on that stream starts only after the write has finished."""
+    import torch
+    with torch.cuda.stream(stream):
+        flush.fill_(1.0)
 
 
 def max_over_ranks(values, device, dist=None):
@@ -159,48 +178,33 @@ def _even_sample(wl, n_target):
         k += 1
 
 
-def _oracle_cost(wl, xl):
-    """Oracle step time as a + b * nodes (a: the grid work of a step), from two small samples."""
-    from oracle import oracle as O
-    pts = []
-    for n_target in (3000, 40000):
-        sel, n = _even_sample(wl, n_target)
-        t0 = time.perf_counter()
-        O.oracle_step(wl, x_local=xl, instances=sel)
-        pts.append((n, time.perf_counter() - t0))
-    (n1, t1), (n2, t2) = pts
-    b = max((t2 - t1) / max(n2 - n1, 1), 1e-9)
-    return max(t1 - b * n1, 0.0), b
-
-
 def run_reference(args, rank, world):
-    """The FP64 CPU oracle on the same workload (rank 0 only).
+    """The FP64 CPU oracle on the same workload (rank 0 only), over all host cores.
 
     Each step is one oracle coupling step (forces, spread, interpolation, sums)
-    over a sample of the particles sized so that the warm-up and timed steps
-    together take about REF_BUDGET_S seconds; the whole suspension when that fits."""
+    run by the multi-core timing driver around the unchanged oracle functions
+    (cpu_baseline_parallel) over the whole workload, or over an evenly spaced
+    sample of its particles when --warmup + --steps whole steps would take
+    more than about REF_BUDGET_S seconds."""
     if rank != 0:
         return
+    import dataclasses
     import ifem_workloads as W
     from oracle import oracle as O
     O.build()
     wl = W.make(args.workload)
-    xl = wl.x_local_all(np.float32).astype(np.float64)
     N = wl.n_nodes
-    a, b = _oracle_cost(wl, xl)
+    probe = cpu_baseline_parallel(wl, steps=1, warmup=1)
+    per_node = probe["step_s"][0] / N
     per_step = REF_BUDGET_S / max(1, args.steps + max(0, args.warmup))
-    sel, n_sel = _even_sample(wl, int(max(0.0, per_step - a) / b))
-    for _ in range(max(0, args.warmup)):
-        O.oracle_step(wl, x_local=xl, instances=sel)
-    ts = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        O.oracle_step(wl, x_local=xl, instances=sel)
-        ts.append(time.perf_counter() - t0)
-    t = float(np.mean(ts))
+    sel, n_sel = _even_sample(wl, int(per_step / per_node))
+    sub = wl if n_sel == N else dataclasses.replace(wl, instances=[wl.instances[i] for i in sel])
+    r = cpu_baseline_parallel(sub, steps=args.steps, warmup=max(1, args.warmup))
+    t = float(np.mean(r["step_s"]))
     val = n_sel / t
     sample = (f"{len(sel)} of {len(wl.instances)} particles evenly spaced ({n_sel} of {N} nodes), one full "
-              f"oracle step (forces + spread + interp + sums) on the whole grid per timed step, single thread")
+              f"oracle step (forces + spread + interp + sums) on the whole grid per timed step, "
+              f"{r['cores']} host threads over the unchanged single-threaded oracle functions")
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "nodes/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
@@ -208,10 +212,39 @@ def run_reference(args, rank, world):
         "config": {"workload": WORKLOADS[args.workload], "nodes": N,
                    "grid": [bx.n for bx in wl.boxes] if len(wl.boxes) > 1 else wl.boxes[0].n,
                    "sample_nodes": n_sel},
-        "cpu_baseline": {"value": val, "unit": "nodes/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": val, "unit": "nodes/s", "cores": r["cores"], "kind": "oracle", "sample": sample,
+                         "host": r["host"]},
         "e2e": {"value": val, "unit": "nodes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def host_description():
+    """The host CPU: model name (lscpu, else /proc/cpuinfo, else platform) and usable cores."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count() or 1
+    return {"cpu_model": model or platform.processor() or platform.machine(), "machine": platform.machine(),
+            "nproc": cores}
 
 
 def cpu_baseline_sample(wl):
@@ -230,6 +263,120 @@ def cpu_baseline_sample(wl):
     return {"value": wl.n_nodes / t, "unit": "nodes/s", "cores": 1, "kind": "oracle",
             "sample": f"the whole workload ({wl.n_nodes} nodes), {len(ts)} full oracle steps (forces + spread + "
                       f"interp + sums), single thread, {sum(ts):.1f} s"}
+
+
+# ---- the oracle over all host cores (a timing driver around the unchanged,
+# single-threaded oracle functions)
+_SUMS_WL = {}
+
+
+def _sums_init(chunks):
+    global _SUMS_WL
+    _SUMS_WL = chunks
+
+
+def _sums_task(args):
+    """Per-particle FP64 sums of one chunk of particles (runs in a worker process)."""
+    from oracle import oracle as O
+    c, xl, F, v = args
+    return O.reductions(_SUMS_WL[c], xl, F, v)
+
+
+def _chunks_by_nodes(wl, parts):
+    """Contiguous particle ranges with about equal node counts."""
+    off = wl.node_offsets()
+    N = int(off[-1])
+    bounds = [0]
+    for p in range(1, parts):
+        bounds.append(int(np.searchsorted(off, p * N / parts)))
+    bounds.append(len(wl.instances))
+    return [(a, b) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+
+
+def cpu_baseline_parallel(wl, threads=None, min_s=3.0, max_steps=8, steps=None, warmup=1):
+    """The oracle's coupling step over all host cores: one thread per chunk of
+    particles (contiguous, equal node counts) runs the oracle's element and
+    bending forces, its spreading into a private grid per chunk and its
+    interpolation (the C calls release the interpreter lock); the private
+    grids are summed in chunk order (fixed order, split over the threads by
+    slabs); the per-particle FP64 sums, which the oracle takes with
+    math.fsum under the interpreter lock, run in a process pool (spawn). The
+    oracle itself is unchanged and single-threaded."""
+    import concurrent.futures as cf
+    import dataclasses
+    import multiprocessing as mp
+    from oracle import oracle as O
+    O.build()
+    host = host_description()
+    P = threads or host["nproc"]
+    xl = wl.x_local_all(np.float32).astype(np.float64)
+    off = wl.node_offsets()
+    chunks = _chunks_by_nodes(wl, P)
+    light = {c: dataclasses.replace(wl, instances=[dataclasses.replace(i, x_local=np.zeros((0, 3)))
+                                                   for i in wl.instances[a:b]], u=[])
+             for c, (a, b) in enumerate(chunks)}
+    origins = wl.origins_per_node()
+    box_of = np.concatenate([np.full(off[i + 1] - off[i], inst.box) for i, inst in enumerate(wl.instances)])
+
+    def local_work(c):
+        a, b = chunks[c]
+        lo, hi = int(off[a]), int(off[b])
+        F = np.zeros((hi - lo, 3))
+        for ii in range(a, b):
+            F[off[ii] - lo:off[ii + 1] - lo] = O.template_forces(wl.templates[wl.instances[ii].tmpl],
+                                                                 xl[off[ii]:off[ii + 1]])
+        xa = origins[lo:hi] + xl[lo:hi]
+        v = np.zeros_like(F)
+        grids = {}
+        for bi, bx in enumerate(wl.boxes):
+            rows = np.flatnonzero(box_of[lo:hi] == bi)
+            if rows.size:
+                grids[bi] = O.spread(xa[rows], F[rows], bx.n, bx.L)
+                v[rows] = O.interp(xa[rows], wl.u[bi], bx.n, bx.L)
+        return F, v, grids
+
+    def grid_sum(parts, out, s0, s1):
+        out[s0:s1] = 0.0
+        for g in parts:        # chunk order: fixed summation order
+            out[s0:s1] += g[s0:s1]
+
+    ctx = mp.get_context("spawn")
+    ts = []
+    with cf.ThreadPoolExecutor(P) as tp, cf.ProcessPoolExecutor(P, mp_context=ctx, initializer=_sums_init,
+                                                                initargs=(light,)) as pp:
+        fields = [np.zeros((3, bx.n, bx.n, bx.n)) for bx in wl.boxes]
+        warm = max(1, warmup)   # the first step starts the worker processes: never timed
+
+        def more():
+            if steps is not None:
+                return len(ts) < steps
+            return (sum(ts) < min_s or len(ts) < 2) and len(ts) < max_steps
+
+        while more():
+            t0 = time.perf_counter()
+            res = list(tp.map(local_work, range(len(chunks))))
+            jobs = []
+            for bi, bx in enumerate(wl.boxes):
+                parts = [r[2][bi].reshape(-1) for r in res if bi in r[2]]
+                flat = fields[bi].reshape(-1)
+                step = -(-flat.size // P)
+                jobs += [tp.submit(grid_sum, parts, flat, s0, min(s0 + step, flat.size))
+                         for s0 in range(0, flat.size, step)]
+            sums = list(pp.map(_sums_task, [(c, xl[off[a]:off[b]], r[0], r[1])
+                                            for c, ((a, b), r) in enumerate(zip(chunks, res))]))
+            for j in jobs:
+                j.result()
+            if warm == 0:
+                ts.append(time.perf_counter() - t0)
+            else:
+                warm -= 1
+            del res, sums
+    t = float(np.mean(ts))
+    return {"value": wl.n_nodes / t, "unit": "nodes/s", "cores": P, "kind": "oracle",
+            "sample": (f"the whole workload ({wl.n_nodes} nodes), {len(ts)} full oracle steps on {P} threads "
+                       f"(forces, spread into per-chunk private grids, interp; grids summed in chunk order; "
+                       f"per-particle sums in {P} processes), {sum(ts):.1f} s wall"),
+            "host": host, "step_s": ts}
 
 
 def time_extras(wl, I, torch, dev, flush, T, reps=20, warm=3):
@@ -288,7 +435,7 @@ def time_extras(wl, I, torch, dev, flush, T, reps=20, warm=3):
     for name, (call, nbytes) in calls.items():
         ts = []
         for it in range(warm + reps):
-            flush.fill_(1.0)
+            flush_l2(flush, s)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(s)
             call()
@@ -367,19 +514,23 @@ def main():
         step(torch.cuda.current_stream())
     torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        flush.fill_(1.0)
-        g.replay()
-    torch.cuda.synchronize()
+    # clock samples: from before the headline steps to after the last timed
+    # GPU loop (the headline region alone can be shorter than one sample)
     clocks = Clocks(local)
+    clocks.start()
+    time.sleep(1.0)   # nvidia-smi's first sample lands before the timed steps
+    for _ in range(args.warmup):
+        flush_l2(flush, stream)
+        with torch.cuda.stream(stream):
+            g.replay()
+    torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
     times = []
     t_wall0 = time.perf_counter()
     for _ in range(args.steps):
-        flush.fill_(1.0)
+        flush_l2(flush, stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         with torch.cuda.stream(stream):
@@ -391,7 +542,6 @@ def main():
     if dist:
         dist.barrier()
     wall = time.perf_counter() - t_wall0
-    ck = clocks.stop()
     t_ms = max_over_ranks([float(np.mean(times))], dev, dist)[0]
     value = job_throughput(N, world, t_ms)
 
@@ -400,7 +550,7 @@ def main():
     stages = {k: [] for k in ("bin", "forces", "spread", "interp", "reduce")}
     fp = cpp.zeros_grid()
     for it in range(args.warmup + args.steps):
-        flush.fill_(1.0)
+        flush_l2(flush, stream)
         with torch.cuda.stream(stream):
             I.ifem_step_coupling(cpp.ctx, cpp.batch, cpp.grid, x, u, F, fp, v, red, 0, stream)
         ms = I.ifem_stage_times(cpp.ctx)
@@ -420,6 +570,7 @@ def main():
               key=lambda k: stage_ms[k])
     achieved = ab[dom] / (stage_ms[dom] * 1e-3) / 1e9
     step_gbs = ab["step"] / (t_ms * 1e-3) / 1e9
+    step_gbs_F = ab["step_with_F"] / (t_ms * 1e-3) / 1e9
 
     # end to end through the C ABI with host buffers (pinned): ifem_step_coupling_host
     # copies x in, runs the step and copies v and the sums out, all inside the
@@ -441,7 +592,7 @@ def main():
     def time_e2e(fn):
         ts = []
         for it in range(args.warmup + args.steps):
-            flush.fill_(1.0)
+            flush_l2(flush, stream)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             with torch.cuda.stream(stream):
@@ -472,7 +623,7 @@ def main():
         torch.cuda.synchronize()
         ts = []
         for _ in range(3):
-            flush.fill_(1.0)
+            flush_l2(flush, stream)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             I.ifem_step_coupling(c64.ctx, c64.batch, c64.grid, x64, u64, F64, f64, v64, None, 0, stream)
@@ -489,10 +640,14 @@ def main():
         fp64 = {"value": N / (t64 * 1e-3), "unit": "nodes/s", "ms_per_step": t64, "tile": I.ifem_ctx_tile(c64.ctx),
                 "fp32_rel_l2_vs_fp64": {"F": eF, "v": ev}}
         c64.close()
+    ck = clocks.stop()
 
     if rank != 0:
         return
-    cpu = None if args.no_cpu else cpu_baseline_sample(wl)
+    cpu = None
+    if not args.no_cpu:
+        cpu = cpu_baseline_parallel(wl)
+        cpu["single_thread"] = cpu_baseline_sample(wl)
     # bin (count, 3 scan, fill), forces, spread, interp (or one fused launch), 2 reductions
     launches_per_step = 5 + 1 + (1 if fused else 2) + 2
     if scatter == I.IFEM_SCATTER_DET:
@@ -508,6 +663,9 @@ def main():
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "hbm_gbs_step": step_gbs,
         "step_roofline_frac": step_gbs / hbm,
+        "step_algorithmic_bytes": {"per_step": ab["step"], "formula": "24N + 12T (x read, v written; u read, "
+                                   "f read + written over the touched values)",
+                                   "with_F_round_trip": ab["step_with_F"], "hbm_gbs_with_F": step_gbs_F},
         "stage_ms": stage_ms,
         "touched_values": T, "pairs": P,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -515,7 +673,9 @@ def main():
                      "limiter": ({"unit": NCU_LIMITER[dom][0], "frac_of_peak": NCU_LIMITER[dom][1],
                                   "source": "ncu capture on this workload (profiles/)"}
                                  if args.workload == "C4" and dom in NCU_LIMITER else None), "peak_kind": peak_kind,
-                     "algorithmic_bytes": ab[dom]},
+                     "algorithmic_bytes": ab[dom],
+                     "bytes_formula": {"spread+interp": "36N + 12T", "spread": "24N + 4N + 8T",
+                                       "interp": "24N + 4N + 4T", "forces": "24N", "bin": "24N + 4N"}.get(dom)},
         "cpu_baseline": cpu,
         "e2e": {"value": job_throughput(N, world, e2e_ms), "unit": "nodes/s", "h2d_bytes_per_step": 12 * N,
                 "d2h_bytes_per_step": 12 * N + 8 * red.numel(), "ms_per_step": e2e_ms,

@@ -57,6 +57,10 @@
  *   ifem_sync_status() reads. No kernel traps.
  * Errors. Functions return ifem_status; IFEM_OK = 0, negative on error;
  *   ifem_last_error(ctx) gives a message for the last failed call on ctx.
+ * Current device. A call that touches the GPU makes the context's device
+ *   (ifem_config.device) current on the calling thread while it runs and
+ *   restores the thread's previous current device before returning, so the
+ *   caller's device selection is left as it was.
  */
 #ifndef IFEM_H
 #define IFEM_H
@@ -424,18 +428,19 @@ int ifem_step_coupling_host(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void 
  * ifem_compute_forces: (dF/dx)^T g = -H g (H symmetric). */
 int ifem_force_hvp(ifem_ctx ctx, ifem_batch b, const void *x, const void *w, void *Hw, void *stream);
 
-/* ifem_compute_forces without any allocation in the call (the paper has no
- * counterpart: this is a deployment variant of Algorithm step 1).
- * Some callers must not allocate device memory while they run: code recorded
- * into a CUDA graph under global stream capture, where cudaMalloc is not
- * allowed; hosts that hand all device memory to their own pool or allocator
- * up front; real-time loops that forbid allocation after start-up. This entry
- * point computes the same forces as ifem_compute_forces through the
- * deterministic element-buffer path (per-element forces, then a per-node sum
- * in ascending element order, then the bending passes), taking its scratch
- * from one fixed array of 32 MiB in device memory that the library declares
- * at file scope: every GPU that loads libifem holds it until the process
- * exits. It calls no cudaMalloc, cudaFree or allocating library routine.
+/* ifem_compute_forces without any allocation in the call. The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate.
+ * Some callers of this library cannot call cudaMalloc: hosts that hand all
+ * device memory to their own pool or allocator at start-up (a second
+ * allocator fails or fragments their memory), and real-time loops that forbid
+ * allocation once running (cudaMalloc may synchronise the device and takes
+ * unbounded time). This entry point computes the forces of
+ * ifem_compute_forces through the deterministic element-buffer path
+ * (per-element forces, then a per-node sum in ascending element order, then
+ * the bending passes), taking its scratch from one fixed array of 32 MiB in
+ * device memory that the library declares at file scope: every GPU that
+ * loads libifem holds it until the process exits. It calls no cudaMalloc,
+ * cudaFree or allocating library routine. The caller still passes x and F.
  *   Limit: 12 reals per element plus 6 reals per node (reals of the
  *   context's precision; the node part starts at a 256-byte boundary) must
  *   fit in 32 MiB, e.g. about 600k triangles in IFEM_FP32; larger batches
@@ -450,7 +455,8 @@ int ifem_force_hvp(ifem_ctx ctx, ifem_batch b, const void *x, const void *w, voi
  * Arguments, layouts, stream semantics and status reporting are those of
  * ifem_compute_forces; the FP32 results are deterministic but may differ in
  * the last bits from ifem_compute_forces (this path uses no fused
- * multiply-add). */
+ * multiply-add). Launch errors are reported for the first launch that failed;
+ * no kernel after it is queued. */
 int ifem_compute_forces_noalloc(ifem_ctx ctx, ifem_batch b, const void *x, void *F, void *stream);
 
 #ifdef __cplusplus

@@ -71,6 +71,7 @@ extern "C" int ifem_config_default(ifem_config *cfg)
 
 extern "C" int ifem_ctx_create(const ifem_config *cfg, ifem_ctx *out)
 {
+    DeviceScope ifem_device_scope_(cfg ? cfg->device : -1);
     ifem_ctx ctx = nullptr;
     if (!cfg || !out)
         return IFEM_ERR_ARG;
@@ -130,6 +131,7 @@ extern "C" int ifem_ctx_create(const ifem_config *cfg, ifem_ctx *out)
 
 extern "C" int ifem_ctx_destroy(ifem_ctx ctx)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     if (!ctx)
         return IFEM_ERR_ARG;
     for (int i = 0; i < 6; ++i)
@@ -153,6 +155,7 @@ extern "C" int ifem_ctx_tile(ifem_ctx ctx) { return ctx ? ctx->tile : IFEM_ERR_A
 
 extern "C" int ifem_stage_times(ifem_ctx ctx, double *ms)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     if (!ctx || !ms || !ctx->ev_ok || !ctx->ev_recorded)
         return fail(ctx, IFEM_ERR_ARG, "stage_times: profiling off or no step recorded");
     CK(cudaEventSynchronize(ctx->ev[5]));
@@ -176,6 +179,7 @@ static void mark(ifem_ctx ctx, int i, void *stream)
 
 extern "C" int ifem_sync_status(ifem_ctx ctx, ifem_stats *out)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     if (!ctx)
         return IFEM_ERR_ARG;
     CK(cudaSetDevice(ctx->cfg.device));
@@ -332,6 +336,7 @@ extern "C" int ifem_tmpl_create_membrane(ifem_ctx ctx, int n_nodes, int n_tris, 
                                          const double *X_ref, int law, const ifem_membrane_params *p,
                                          ifem_tmpl *out)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     if (!ctx || !out || !tris || !X_ref || !p || n_nodes < 3 || n_tris < 1)
         return fail(ctx, IFEM_ERR_ARG, "membrane template: null pointer or empty mesh");
     *out = nullptr;
@@ -380,6 +385,7 @@ extern "C" int ifem_tmpl_create_membrane(ifem_ctx ctx, int n_nodes, int n_tris, 
 extern "C" int ifem_tmpl_create_solid(ifem_ctx ctx, int n_nodes, int n_tets, const int32_t *tets,
                                       const double *X_ref, const ifem_solid_params *p, ifem_tmpl *out)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     if (!ctx || !out || !tets || !X_ref || !p || n_nodes < 4 || n_tets < 1)
         return fail(ctx, IFEM_ERR_ARG, "solid template: null pointer or empty mesh");
     *out = nullptr;
@@ -411,6 +417,7 @@ extern "C" int ifem_tmpl_create_solid(ifem_ctx ctx, int n_nodes, int n_tets, con
 
 extern "C" int ifem_tmpl_destroy(ifem_tmpl t)
 {
+    IFEM_DEVICE_SCOPE(t ? t->ctx : nullptr);
     if (!t)
         return IFEM_ERR_ARG;
     cudaFree(t->d_elems);
@@ -480,6 +487,7 @@ static void split_origins(ifem_batch b, ifem_grid g)
 extern "C" int ifem_batch_create(ifem_ctx ctx, int n_tmpl, const ifem_tmpl *tmpls, int n_inst,
                                  const ifem_instance_desc *inst, ifem_grid grid, ifem_batch *out)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     if (!ctx || !out || !tmpls || n_tmpl < 1 || n_inst < 0 || (n_inst > 0 && !inst) || !grid)
         return fail(ctx, IFEM_ERR_ARG, "batch: null pointer or bad counts");
     *out = nullptr;
@@ -575,6 +583,7 @@ static void ws_free(Workspace &ws)
 
 extern "C" int ifem_batch_destroy(ifem_batch b)
 {
+    IFEM_DEVICE_SCOPE(b ? b->ctx : nullptr);
     if (!b)
         return IFEM_ERR_ARG;
     ws_free(b->ws);
@@ -592,6 +601,7 @@ extern "C" int ifem_batch_instances(ifem_batch b) { return b ? (int)b->inst.size
 
 extern "C" int ifem_batch_set_origins(ifem_batch b, const double *origins)
 {
+    IFEM_DEVICE_SCOPE(b ? b->ctx : nullptr);
     if (!b || !origins)
         return IFEM_ERR_ARG;
     ifem_ctx ctx = b->ctx;
@@ -851,6 +861,7 @@ static int do_reduce(ifem_ctx ctx, ifem_batch b, const void *x, const void *F, c
 // ------------------------------------------------------------ compute
 extern "C" int ifem_compute_forces(ifem_ctx ctx, ifem_batch b, const void *x, void *F, void *stream)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     int rc = check_call(ctx, b, nullptr);
     if (rc != IFEM_OK)
         return rc;
@@ -861,6 +872,7 @@ extern "C" int ifem_compute_forces(ifem_ctx ctx, ifem_batch b, const void *x, vo
 
 extern "C" int ifem_force_hvp(ifem_ctx ctx, ifem_batch b, const void *x, const void *w, void *Hw, void *stream)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     int rc = check_call(ctx, b, nullptr);
     if (rc != IFEM_OK)
         return rc;
@@ -872,6 +884,7 @@ extern "C" int ifem_force_hvp(ifem_ctx ctx, ifem_batch b, const void *x, const v
 extern "C" int ifem_spread(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *F, void *f,
                            int flags, void *stream)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     int rc = check_call(ctx, b, g);
     if (rc != IFEM_OK)
         return rc;
@@ -898,6 +911,7 @@ static LagrangeArgs lagrange_args(ifem_ctx ctx, ifem_batch b, void *x, void *str
 extern "C" int ifem_ab2_update(ifem_ctx ctx, ifem_batch b, void *x, const void *v, const void *v_prev, double dt,
                                void *stream)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     int rc = check_call(ctx, b, nullptr);
     if (rc != IFEM_OK)
         return rc;
@@ -915,6 +929,7 @@ extern "C" int ifem_ab2_update(ifem_ctx ctx, ifem_batch b, void *x, const void *
 
 extern "C" int ifem_volumes(ifem_ctx ctx, ifem_batch b, const void *x, double *vol, void *stream)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     int rc = check_call(ctx, b, nullptr);
     if (rc != IFEM_OK)
         return rc;
@@ -929,6 +944,7 @@ extern "C" int ifem_volumes(ifem_ctx ctx, ifem_batch b, const void *x, double *v
 extern "C" int ifem_volume_correct(ifem_ctx ctx, ifem_batch b, void *x, const double *V0, double *lambda,
                                    void *stream)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     int rc = check_call(ctx, b, nullptr);
     if (rc != IFEM_OK)
         return rc;
@@ -944,6 +960,7 @@ extern "C" int ifem_volume_correct(ifem_ctx ctx, ifem_batch b, void *x, const do
 extern "C" int ifem_indicator_source(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, void *G, int flags,
                                      void *stream)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     int rc = check_call(ctx, b, g);
     if (rc != IFEM_OK)
         return rc;
@@ -966,6 +983,7 @@ extern "C" int ifem_indicator_source(ifem_ctx ctx, ifem_batch b, ifem_grid g, co
 extern "C" int ifem_interpolate_cc(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *field, int ncomp,
                                    const void *x, void *out, void *stream)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     int rc = check_call(ctx, b, g);
     if (rc != IFEM_OK)
         return rc;
@@ -983,6 +1001,7 @@ extern "C" int ifem_interpolate_cc(ifem_ctx ctx, ifem_batch b, ifem_grid g, cons
 extern "C" int ifem_fluid_stress_forces(ifem_ctx ctx, ifem_batch b, const void *x, const void *u, const void *C,
                                         const ifem_fluid_params *p, void *F, int flags, void *stream)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     int rc = check_call(ctx, b, nullptr);
     if (rc != IFEM_OK)
         return rc;
@@ -1011,6 +1030,7 @@ extern "C" int ifem_fluid_stress_forces(ifem_ctx ctx, ifem_batch b, const void *
 extern "C" int ifem_interpolate(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *u, const void *x, void *v,
                                 void *stream)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     int rc = check_call(ctx, b, g);
     if (rc != IFEM_OK)
         return rc;
@@ -1029,6 +1049,7 @@ extern "C" int ifem_interpolate(ifem_ctx ctx, ifem_batch b, ifem_grid g, const v
 extern "C" int ifem_reduce(ifem_ctx ctx, ifem_batch b, const void *x, const void *F, const void *v, double *red,
                            void *stream)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     int rc = check_call(ctx, b, nullptr);
     if (rc != IFEM_OK)
         return rc;
@@ -1245,6 +1266,7 @@ static int check_step(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, co
 extern "C" int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *u, void *F,
                                   void *f, void *v, double *red, int flags, void *stream)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     int rc = check_step(ctx, b, g, x, u, F, f, v, flags, "step_coupling");
     if (rc != IFEM_OK)
         return rc;
@@ -1255,6 +1277,7 @@ extern "C" int ifem_step_coupling_ab2(ifem_ctx ctx, ifem_batch b, ifem_grid g, c
                                       void *F, void *f, void *v, double *red, int flags, const void *v_prev,
                                       double dt, void *x_new, void *stream)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     int rc = check_step(ctx, b, g, x, u, F, f, v, flags, "step_coupling_ab2");
     if (rc != IFEM_OK)
         return rc;
@@ -1281,6 +1304,7 @@ extern "C" int ifem_step_coupling_host(ifem_ctx ctx, ifem_batch b, ifem_grid g, 
                                        const void *u, void *F, void *f, void *v, void *v_host, double *red,
                                        double *red_host, int flags, void *stream)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     int rc = check_step(ctx, b, g, x, u, F, f, v, flags, "step_coupling_host");
     if (rc != IFEM_OK)
         return rc;
@@ -1376,6 +1400,7 @@ static int autotune(ifem_ctx ctx, ifem_batch b, const void *x, void *stream)
 
 extern "C" int ifem_prepare(ifem_ctx ctx, ifem_batch b, const void *x, void *stream)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     int rc = check_call(ctx, b, nullptr);
     if (rc != IFEM_OK)
         return rc;

@@ -81,6 +81,32 @@ struct ifem_batch_s {
     Workspace ws;
 };
 
+// Makes `dev` the calling thread's current device for the lifetime of the
+// object and then gives the caller's previous current device back, so that an
+// entry point leaves the caller's device selection as it found it (dev < 0:
+// nothing to do). The entry points' own cudaSetDevice calls inside the scope
+// select the same device again.
+struct DeviceScope {
+    int prev = -1, dev = -1;
+    explicit DeviceScope(int d) : dev(d)
+    {
+        if (dev < 0)
+            return;
+        if (cudaGetDevice(&prev) != cudaSuccess)
+            prev = -1;
+        if (prev != dev)
+            cudaSetDevice(dev);
+    }
+    ~DeviceScope()
+    {
+        if (dev >= 0 && prev >= 0 && prev != dev)
+            cudaSetDevice(prev);
+    }
+    DeviceScope(const DeviceScope &) = delete;
+    DeviceScope &operator=(const DeviceScope &) = delete;
+};
+#define IFEM_DEVICE_SCOPE(c) DeviceScope ifem_device_scope_((c) ? (c)->cfg.device : -1)
+
 inline DevBatch dev_batch(ifem_batch b)
 {
     DevBatch d{};

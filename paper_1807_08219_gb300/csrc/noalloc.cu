@@ -28,12 +28,20 @@ cudaError_t launch(const DevBatch &b, const real *x, real *F, unsigned char *scr
     real *ebuf = reinterpret_cast<real *>(scratch);
     real *bbuf = reinterpret_cast<real *>(scratch + bend_off);
     dim3 ge((b.max_elems + 255) / 256, b.n_inst), gn((b.max_nodes + 255) / 256, b.n_inst);
+    // each launch is checked before the next is queued: a later kernel must
+    // not read scratch that a failed launch never wrote, and the first error
+    // is the one reported
     elem_force_kernel<real, false><<<ge, 256, 0, s>>>(b, x, nullptr, ebuf, status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
     node_gather_kernel<real><<<gn, 256, 0, s>>>(b, ebuf, F);
-    if (b.any_bending) {
-        bend_pass1_kernel<real><<<gn, 256, 0, s>>>(b, x, bbuf);
-        bend_pass2_kernel<real><<<gn, 256, 0, s>>>(b, x, bbuf, F);
-    }
+    if ((e = cudaGetLastError()) != cudaSuccess || !b.any_bending)
+        return e;
+    bend_pass1_kernel<real><<<gn, 256, 0, s>>>(b, x, bbuf);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    bend_pass2_kernel<real><<<gn, 256, 0, s>>>(b, x, bbuf, F);
     return cudaGetLastError();
 }
 
@@ -41,6 +49,7 @@ cudaError_t launch(const DevBatch &b, const real *x, real *F, unsigned char *scr
 
 extern "C" int ifem_compute_forces_noalloc(ifem_ctx ctx, ifem_batch b, const void *x, void *F, void *stream)
 {
+    IFEM_DEVICE_SCOPE(ctx);
     if (!ctx || !b || b->ctx != ctx) {
         if (ctx)
             ctx->err = "compute_forces_noalloc: null or foreign batch";

@@ -9,20 +9,38 @@ import ifem_workloads as W
 
 
 def test_algorithmic_bytes_closed_forms():
+    """The per-unit bytes of the hot path: a fused transfer launch moves x and
+    F in and v out (36 B per node) and reads u, reads and writes f once per
+    touched lattice value (12 B); the coupling step as one operation moves x
+    in and v out (24 B per node) plus the same 12 B per touched value; the F
+    round trip adds 24 B per node and is reported separately."""
     import bench
     N, T = 1_332_200, 18_680_000
     ab = bench.algorithmic_bytes(N, T, 0)
-    # fused transfer: x, F read + v written (36N), own-node list (4N), u read + f read and written (12T)
-    assert ab["spread+interp"] == 40 * N + 12 * T
-    # whole step: x, v, F written and read, u read, f read and written
-    assert ab["step"] == 48 * N + 12 * T
+    assert ab["spread+interp"] == 36 * N + 12 * T
+    assert ab["step"] == 24 * N + 12 * T
+    assert ab["step_with_F"] == 48 * N + 12 * T
     assert ab["forces"] == 24 * N and ab["reduce"] == 36 * N
     # with candidate lists the spread reads one entry per (tile, node) pair
     P = 3 * N
     assert bench.algorithmic_bytes(N, T, P)["spread"] == 24 * N + 4 * P + 8 * T
-    # FP64 doubles every real-valued byte, not the int32 lists
+    # FP64 doubles every real-valued byte
     ab8 = bench.algorithmic_bytes(N, T, 0, real=8)
-    assert ab8["spread+interp"] == 2 * (36 * N + 12 * T) + 4 * N
+    assert ab8["spread+interp"] == 2 * (36 * N + 12 * T)
+    # C4 figures: 0.272 GB per fused launch, 0.256 GB per step
+    assert ab["spread+interp"] == pytest.approx(272.1e6, rel=1e-3)
+    assert ab["step"] == pytest.approx(256.1e6, rel=1e-3)
+
+
+def test_chunks_by_nodes_cover_every_particle_once():
+    import bench
+    w = W.make("C2")
+    w7 = dataclasses.replace(w, instances=[w.instances[0]] * 7)
+    for parts in (1, 3, 7, 16):
+        ch = bench._chunks_by_nodes(w7, parts)
+        assert ch[0][0] == 0 and ch[-1][1] == 7
+        assert all(a < b for a, b in ch) and all(ch[i][1] == ch[i + 1][0] for i in range(len(ch) - 1))
+        assert len(ch) == min(parts, 7)
 
 
 def test_even_sample_reaches_target_evenly():

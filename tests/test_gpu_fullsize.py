@@ -5,7 +5,8 @@ on the suspension also the step with the fused position update and the
 host-array step.
 
 FP64 mode: interpolation and spreading (of the GPU's own forces) bit-exact,
-forces within 1e-12 (bending uses atan2). FP32 mode: the stated relative L2
+forces within 1e-13 relative L2 (the bending angle deficit is taken from a
+different atan2 on each side; the measured error is printed). FP32 mode: the stated relative L2
 tolerances (forces 1e-5, velocities 1e-6, grid field 1e-5).
 """
 import numpy as np
@@ -89,7 +90,9 @@ def test_fullsize_fp64_deterministic(name):
     rc, st, F, v, f = run(wl, 1, 0, 0)
     assert rc == 0, st
     Fo, vo, fo = oracle_parts(wl, F)
-    assert rel_l2(F, Fo) < 1e-12
+    eF = rel_l2(F, Fo)
+    print(f"{name} FP64 forces: rel L2 {eF:.3e} against the oracle")
+    assert eF < 1e-13, eF
     assert np.array_equal(v, vo)
     for a, b in zip(f, fo):
         assert np.array_equal(a, b)

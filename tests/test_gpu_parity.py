@@ -1,8 +1,11 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
 FP64 (deterministic) mode: element forces, nodal sums, spreading and
-interpolation must be bit-identical to the oracle; the bending force (which
-uses atan2) must agree to 1e-12 relative L2.
+interpolation must be bit-identical to the oracle; the bending force must
+agree to 1e-13 relative L2 (the oracle sums the corner angles with one libm
+atan2 each, the GPU takes the angle deficit from one CUDA atan2 of a complex
+product per vertex, and the cotangents from one reciprocal of 2A per
+triangle; the measured error is printed).
 FP32 mode: relative L2 error against the oracle evaluated on the same
 FP32-rounded inputs within 1e-5 (forces, spread field) and 1e-6 (interpolated
 velocities).
@@ -18,6 +21,7 @@ pytestmark = pytest.mark.gpu
 
 FP32, FP64 = 0, 1
 TOL_F, TOL_V, TOL_GRID = 1e-5, 1e-6, 1e-5
+TOL_BEND64 = 1e-13
 
 _cache = {}
 
@@ -59,9 +63,11 @@ def test_fp64_bending_step(kernel):
     w = wl("C2")
     g = run_gpu_step(w, FP64, kernel=kernel)
     o = oracle_step(w, kernel=kernel)
-    assert rel_l2(g["F"], o["F"]) < 1e-12
+    eF, ef = rel_l2(g["F"], o["F"]), rel_l2(g["f"][0], o["f"][0])
+    print(f"C2 FP64 bending step, kernel {kernel}: rel L2 F {eF:.3e}, spread field {ef:.3e}")
+    assert eF < TOL_BEND64, eF
     assert rel_l2(g["v"], o["v"]) == 0.0
-    assert rel_l2(g["f"][0], o["f"][0]) < 1e-12
+    assert ef < TOL_BEND64, ef
 
 
 def test_fp64_deterministic_across_runs():
@@ -158,7 +164,10 @@ def test_hvp_vs_oracle(case, precision):
         o = O.membrane_hvp(tm.law, tm.mu, tm.C, tm.elems, tm.X, x, wvec)
     else:
         o = O.tet_hvp(tm.lam, tm.mu, tm.elems, tm.X, x, wvec)
-    assert rel_l2(g, o) < (1e-12 if precision == FP64 else 1e-4)
+    e = rel_l2(g, o)
+    print(f"{case} HVP {'FP64' if precision == FP64 else 'FP32'}: rel L2 {e:.3e} against the oracle")
+    # FP32: the force tolerance (the HVP is the same element arithmetic, differentiated)
+    assert e < (1e-12 if precision == FP64 else TOL_F), e
 
 
 # ------------------------------------------------------------------ edge cases

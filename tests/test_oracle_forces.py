@@ -218,19 +218,27 @@ def test_bending_vanishes_on_sphere_with_refinement():
 
 
 def test_bending_force_matches_energy_variation_to_discretisation_order():
-    """-sum F . dx against the FD change of the discrete Helfrich energy, on an ellipsoid."""
-    v, f = meshes.icosphere(4)
-    x = v @ np.diag([1.0, 0.8, 0.6]).T
-    kb = 1.0
-    rng = np.random.default_rng(3)
-    # smooth normal-ish perturbation (low mode), well resolved by the mesh
-    dx = (np.sin(2 * x[:, 0]) + np.cos(3 * x[:, 1]))[:, None] * v
-    Fb = O.bending_forces(kb, f, x)
-    eps = 1e-5
-    dE = (O.bending_energy(kb, f, x + eps * dx) - O.bending_energy(kb, f, x - eps * dx)) / (2 * eps)
-    work = -np.sum(Fb * dx)
-    assert work == pytest.approx(dE, rel=0.1)
-    del rng
+    """-sum F . dx against the FD change of the discrete Helfrich energy, on an
+    ellipsoid (semi-axes 1, 0.8, 0.6) under a smooth perturbation. The force
+    is not the exact gradient of the discrete energy, so the two agree to the
+    discretisation order only: 0.82 % at icosphere level 3 and 0.22 % at
+    level 4, shrinking about 4x per refinement (second order). The bounds sit
+    just above those figures, so a missing factor or a dropped term in one of
+    the force's terms fails."""
+    rel = []
+    for lev, bound in ((3, 0.012), (4, 0.004)):
+        v, f = meshes.icosphere(lev)
+        x = v @ np.diag([1.0, 0.8, 0.6]).T
+        kb = 1.0
+        # smooth normal-ish perturbation (low mode), well resolved by the mesh
+        dx = (np.sin(2 * x[:, 0]) + np.cos(3 * x[:, 1]))[:, None] * v
+        Fb = O.bending_forces(kb, f, x)
+        eps = 1e-5
+        dE = (O.bending_energy(kb, f, x + eps * dx) - O.bending_energy(kb, f, x - eps * dx)) / (2 * eps)
+        work = -np.sum(Fb * dx)
+        rel.append(abs(work / dE - 1.0))
+        assert rel[-1] < bound, (lev, rel[-1])
+    assert rel[1] < rel[0] / 3.0, rel
 
 
 def test_bending_scale_invariance():

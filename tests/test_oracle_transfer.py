@@ -200,3 +200,72 @@ def test_interp_second_order_convergence(kernel):
         errs.append(np.abs(O.interp(x, u, n, 1.0, kernel) - exact).max())
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert min(rates) > 1.7, (errs, rates)
+
+
+# ------------------------------------------------ conservation sums (FP64)
+def _sums_workload(parts):
+    """A workload holding only what the per-particle sums read: one template
+    per particle (its node count), instances with the given local positions."""
+    tm = [W.Template(kind="solid", X=np.zeros((len(x), 3)), elems=np.zeros((0, 4), np.int32), law="nh")
+          for x, _ in parts]
+    inst = [W.Instance(tmpl=i, box=0, origin=np.asarray(org, dtype=np.float64), x_local=np.asarray(x, np.float64))
+            for i, (x, org) in enumerate(parts)]
+    return W.Workload(name="sums", templates=tm, instances=inst, boxes=[W.Box(16)], u=[], seed=0)
+
+
+def test_reductions_closed_form_octahedron():
+    """Force and torque balance sums (Sec. "Numerical Implementation"): six
+    nodes at c +- a e_i carry F = w x (x - c) + G. About the centroid the
+    torque is (tr M - M) w with M = sum r r^T = 2 a^2 I, i.e. 4 a^2 w; the
+    uniform part G adds nothing (sum r = 0) and sum F = 6 G. A torque taken
+    about the origin (6 c x G more), a swapped cross product (sign) or a
+    dropped term fails here."""
+    a, c = 0.375, np.array([0.3, -1.25, 2.5])
+    w, G = np.array([0.5, -2.0, 1.5]), np.array([-0.25, 0.75, 1.0])
+    r = np.concatenate([a * np.eye(3), -a * np.eye(3)])
+    x = c + r
+    F = np.cross(w, r) + G
+    v = np.arange(18, dtype=np.float64).reshape(6, 3) * 0.125
+    wl = _sums_workload([(x, [7.0, 0.0, -3.0])])
+    red = O.reductions(wl, x, F, v)[0]
+    np.testing.assert_array_equal(red[0:3], c)
+    np.testing.assert_allclose(red[3:6], 6 * G, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(red[6:9], 4 * a * a * w, rtol=0, atol=1e-14)
+    np.testing.assert_array_equal(red[9:12], v.sum(0))
+
+
+def test_reductions_rigid_rotation_field_about_offset_centroid():
+    """Random cloud made symmetric about an offset centre c (so the centroid
+    is c exactly), F = w x (x - c) + G: the torque about the centroid equals
+    (tr(M) I - M) w, M the second-moment matrix of the offsets, and is
+    independent of G; several particles are summed separately."""
+    rng = np.random.default_rng(11)
+    parts, exp = [], []
+    for p in range(3):
+        h = rng.standard_normal((40, 3))
+        r = np.concatenate([h, -h])
+        c = rng.uniform(-5, 5, 3)
+        w, G = rng.standard_normal(3), rng.standard_normal(3)
+        M = r.T @ r
+        exp.append((c, len(r) * G, (np.trace(M) * np.eye(3) - M) @ w))
+        parts.append((c + r, np.cross(w, r) + G))
+    wl = _sums_workload([(x, rng.uniform(-1, 1, 3)) for x, _ in parts])
+    xl = np.concatenate([x for x, _ in parts])
+    F = np.concatenate([f for _, f in parts])
+    red = O.reductions(wl, xl, F, np.zeros_like(xl))
+    for p, (c, sF, tq) in enumerate(exp):
+        np.testing.assert_allclose(red[p, 0:3], c, rtol=0, atol=1e-13)
+        np.testing.assert_allclose(red[p, 3:6], sF, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(red[p, 6:9], tq, rtol=1e-12, atol=1e-11)
+        assert np.all(red[p, 9:12] == 0.0)
+
+
+def test_reductions_sums_are_correctly_rounded():
+    """The FP64 sums are correctly rounded: 1e16 + 1 - 1e16 ... in any order
+    gives the exact sum (a plain left-to-right loop would lose the 1s)."""
+    x = np.zeros((4, 3))
+    F = np.array([[1e16, 1.0, 3.0], [1.0, -1e16, 3.0], [-1e16, 1e16, 3.0], [1.0, 1.0, 3.0]])
+    wl = _sums_workload([(x, [0.0, 0.0, 0.0])])
+    red = O.reductions(wl, x, F, F)[0]
+    np.testing.assert_array_equal(red[3:6], [2.0, 2.0, 12.0])
+    np.testing.assert_array_equal(red[9:12], [2.0, 2.0, 12.0])

@@ -1,8 +1,9 @@
 """ifem_compute_forces_noalloc against ifem_compute_forces, through the C ABI.
 
-The allocation-free entry point exists for callers that must not allocate
-device memory while they run (graph capture in global mode, hosts that own
-all device memory through their own pool, allocation-free real-time loops).
+The allocation-free entry point exists for callers that cannot call
+cudaMalloc: hosts whose own pool or allocator owns all device memory from
+start-up, and real-time loops that forbid allocation once running (an
+allocation may synchronise the device and take unbounded time).
 It must give the forces of the ordinary entry point: bit-identical in the
 deterministic FP64 mode, within the FP32 tolerance (relative L2 1e-5)
 otherwise, on two calls in a row (the second call reuses the shared scratch
