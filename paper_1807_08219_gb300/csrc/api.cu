@@ -99,6 +99,12 @@ extern "C" int ifem_ctx_create(const ifem_config *cfg, ifem_ctx *out)
     // 64-bit fixed point (slower shared-memory atomics), anything else 32-bit
     if (const char *acc = std::getenv("IFEM_SPREAD_ACC"))
         ctx->acc64 = std::string(acc) == "64" ? 1 : 0;
+    // fused FP32 transfer kernel (tuning knob): the velocity box of each item
+    // is staged in shared memory (transfer_staged_kernel) unless
+    // IFEM_TRANSFER=halo selects the kernel that gathers velocities through L1
+    ctx->staged = 1;
+    if (const char *tr = std::getenv("IFEM_TRANSFER"))
+        ctx->staged = std::string(tr) == "halo" ? 0 : 1;
     if (cudaSetDevice(cfg->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, cfg->device) != cudaSuccess ||
         cudaMalloc((void **)&ctx->d_status, sizeof(unsigned long long) * kStatusWords) != cudaSuccess ||
@@ -675,6 +681,7 @@ static int ws_ensure(ifem_ctx ctx, ifem_batch b, ifem_grid g, int tile)
     if (ctx->cfg.precision == IFEM_FP64 && ctx->cfg.kernel == IFEM_KERNEL_PESKIN4)
         CK(alloc((void **)&w.wtab, sizeof(DetW) * (size_t)std::max<long long>(N, 1)));
     CK(alloc((void **)&w.active, sizeof(int) * (nt + 1)));
+    CK(alloc((void **)&w.own_tiles, sizeof(int) * (nt + 1)));
     CK(alloc((void **)&w.counters, sizeof(int) * 8));
     CK(alloc((void **)&w.scan_blocks, sizeof(int) * 2 * (nb + 1)));
     CK(alloc((void **)&w.red_tile, sizeof(double) * 3 * (nt + 1)));
@@ -743,7 +750,7 @@ static TransferArgs transfer_args(ifem_ctx ctx, ifem_batch b, const void *x, con
     a.support = ctx->cfg.mls_support;
     a.n_sm = ctx->n_sm;
     a.acc64 = ctx->acc64;
-    a.halo = use_halo(ctx);
+    a.halo = use_halo(ctx) ? (ctx->staged ? 2 : 1) : 0;
     a.stream = (cudaStream_t)stream;
     return a;
 }

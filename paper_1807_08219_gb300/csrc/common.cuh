@@ -124,7 +124,9 @@ struct DevWork {
     float4 *own_rec;    // beside own_nodes (FP32 halo path): fractional cell coordinates x, y, z of
                         // the node and, in w, its cell within the tile packed as 8-bit x | y << 8 | z << 16
     int *active;        // tiles with candidate pairs
-    int *counters;      // [0] n_active, [2] work counter, [4] total pairs, [5] total own nodes
+    int *own_tiles;     // tiles with own nodes (FP32 halo path), counters[3] of them
+    int *counters;      // [0] n_active, [2] work counter, [3] tiles with own nodes, [4] total pairs,
+                        // [5] total own nodes
     int *scan_blocks;   // block partial sums for the tile scan
     void *elem_buf;     // per element nodal forces (12 reals per element)
     void *bend_buf;     // per node bending scratch (A, kH, n[3], lap) 6 reals
@@ -344,7 +346,8 @@ struct TransferArgs {
     double support;
     int n_sm;
     int acc64;        // FP32 spread: 64-bit (1) or 32-bit (0) fixed-point accumulators
-    int halo;         // FP32 Peskin spread with halo scatter (IFEM_SCATTER_ATOMIC)
+    int halo;         // FP32 Peskin spread with halo scatter (IFEM_SCATTER_ATOMIC): 1; 2 with the
+                      // velocity box staged in shared memory when interpolation is fused
     int use_wtab;     // FP64 Peskin interpolation: read the stencils the binning of x tabulated
     const void *vp;   // fused position update (halo spread + interpolation only):
     void *xn;         //   xn = x + dt (3/2 v - 1/2 vp) when xn is not null

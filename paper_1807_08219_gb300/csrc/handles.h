@@ -23,6 +23,7 @@ struct ifem_ctx_s {
     int ev_recorded = 0;
     int ev_fused = 0;   // the recorded step fused interpolation into the spread
     int acc64 = 0;
+    int staged = 1;   // fused FP32 transfer with the velocity box staged in shared memory
     int tuned = 0;
     cudaStream_t aux[2] = {};   // fork-join streams of ifem_step_coupling
     static constexpr int kForkEvents = 9;

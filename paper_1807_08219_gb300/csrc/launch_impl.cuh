@@ -88,6 +88,10 @@ cudaError_t bin_impl(const TransferArgs &a, int det_sort, int with_cand)
     IFEM_LAUNCH_CHECK();
     bin_kernel<real, true><<<gn, 256, 0, s>>>(b, a.g, w, (const real *)a.x, with_cand);
     IFEM_LAUNCH_CHECK();
+    if (!with_cand) {
+        own_tiles_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(nt, w);
+        IFEM_LAUNCH_CHECK();
+    }
     if (det_sort) {
         sort_segments_kernel<<<a.n_sm * 4, 512, 0, s>>>(w);
         IFEM_LAUNCH_CHECK();
@@ -117,6 +121,19 @@ cudaError_t spread_impl(const TransferArgs &a)
             // with u and v given, interpolation is fused into the spread, and
             // with xn also the position update
             const bool fused = a.u != nullptr && a.v != nullptr;
+            if (fused && a.halo == 2) {
+                auto kp = a.xn ? transfer_staged_kernel<true> : transfer_staged_kernel<false>;
+                const size_t sm = (size_t)pair_smem_bytes(E);
+                cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                int occ = 1;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kp, kStagedThreads, sm);
+                occ = occ < 1 ? 1 : occ;
+                kp<<<a.n_sm * occ, kStagedThreads, sm, s>>>(b, a.g, a.w, (const float *)a.x, (const float *)a.F,
+                                                          (float *)a.f, a.density, (const float *)a.u, (float *)a.v,
+                                                          (const float *)a.vp, (float *)a.xn, (float)a.dt);
+                IFEM_LAUNCH_CHECK();
+                return cudaSuccess;
+            }
             auto kern = !fused ? spread_halo_kernel<false>
                                : (a.xn ? spread_halo_kernel<true, true> : spread_halo_kernel<true>);
             size_t sm = sizeof(int) * (size_t)halo_ints(E);

@@ -807,6 +807,283 @@ __host__ __device__ inline int halo_ints(int E)
 // AB2 = true (with INTERP) also takes the position update of Eq.
 // Bashforth_eqn from the velocity it has just gathered, out of place:
 // xn_d = x_d + dt (3/2 v_d - 1/2 vp_d), rounded as in ab2_kernel.
+// Tiles with own nodes, compacted (FP32 halo path): the fused transfer
+// kernel takes its (tile, lattice) items from this list, so no CTA walks
+// empty tiles. counters[3] receives the number of listed tiles.
+static __global__ void own_tiles_kernel(long long n_tiles, DevWork w)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool has = t < n_tiles && w.own_off[(t + 1) * kOwnSub3] > w.own_off[t * kOwnSub3];
+    const unsigned m = __ballot_sync(0xffffffffu, has);
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == 0 && m)
+        base = atomicAdd(&w.counters[3], __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (has)
+        w.own_tiles[base + __popc(m & ((1u << lane) - 1u))] = (int)t;
+}
+
+// red.shared.add without a compiler memory clobber: for accumulators that
+// no thread reads before the next barrier (the caller places a compiler
+// fence before it).
+__device__ __forceinline__ void red_shared_add_nc(unsigned a, int v)
+{
+    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(v));
+}
+
+__device__ __forceinline__ void cp_async16(unsigned dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Next (tile, lattice) item of the staged transfer kernel (thread 0): items
+// are the three lattices of each listed tile, in list order.
+__device__ __forceinline__ void staged_next(const DevGrid &g, const DevWork &w, int &item, TileInfo &ti,
+                                            BoxDev &B)
+{
+    const int n_items = 3 * w.counters[3];
+    const int it = atomicAdd(&w.counters[2], 1);
+    item = -1;
+    if (it < n_items) {
+        const int q = it / 3;
+        const int tile = w.own_tiles[q];
+        item = 3 * tile + (it - 3 * q);
+        ti = decode_tile(g, tile);
+        B = g.boxes[ti.box];
+    }
+}
+
+__device__ __forceinline__ void cp_async8(unsigned dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(unsigned dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+
+// Periodic wrap of a box coordinate in [-n, 2n): the boxes of a grid have
+// at least 8 cells and the halos at most 4, so one correction suffices.
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// Shared buffers of the fused transfer kernel. A, the spread accumulator,
+// covers the tile plus the halo of spread_halo_kernel (4 cells in x, so
+// that the flush adds 16-byte quads, and 2 in y and z). U, the staged
+// velocities, covers exactly the cells the stencils read, 2 cells on every
+// side of the tile: rows of ex + 4 values from x = sx - 2, plane pitch 12
+// floats above the plane size. U starts 8 bytes past a 16-byte boundary, so
+// that the values of x = sx .. sx + ex - 1 fill 16-byte quads. Both rounded
+// to 16 bytes; the pair fits three CTAs per SM for 16-cell tiles.
+constexpr int kStagedThreads = 128;
+__host__ __device__ inline int pair_buf_bytes(int E) { return ((halo_ints(E) * 4 + 15) / 16) * 16; }
+__host__ __device__ inline int pair_u_px(int ex) { return ex + 4; }
+__host__ __device__ inline int pair_u_pp(int ey, int pxu) { return pxu * (ey + 4) + 12; }
+__host__ __device__ inline int pair_u_bytes(int E)
+{
+    return ((8 + 4 * pair_u_pp(E, pair_u_px(E)) * (E + 4) + 15) / 16) * 16;
+}
+__host__ __device__ inline int pair_smem_bytes(int E) { return pair_u_bytes(E) + pair_buf_bytes(E); }
+
+// One (tile, lattice) item of the fused transfer kernel, in registers.
+struct PairItem {
+    int item, tile, d;
+    int sx, sy, sz, ex, ey, ez;
+    int n, bx, by, bz, px, pp;
+    int pxu, ppu;   // pitches of the U box
+    long long grid_off;
+    float sd;
+    double box_scale;
+};
+__device__ __forceinline__ PairItem pair_item(int item, const TileInfo &ti, const BoxDev &B, int density)
+{
+    PairItem it;
+    it.item = item;
+    it.tile = item / 3;
+    it.d = item - 3 * it.tile;
+    it.sx = ti.start[0];
+    it.sy = ti.start[1];
+    it.sz = ti.start[2];
+    it.ex = ti.edge[0];
+    it.ey = ti.edge[1];
+    it.ez = ti.edge[2];
+    it.n = B.n;
+    it.bx = it.ex + 2 * kHaloX;
+    it.by = it.ey + 2 * kHaloYZ;
+    it.bz = it.ez + 2 * kHaloYZ;
+    it.px = halo_px(it.bx);
+    it.pp = halo_pp(it.by, it.px);
+    it.pxu = pair_u_px(it.ex);
+    it.ppu = pair_u_pp(it.ey, it.pxu);
+    it.grid_off = B.grid_off;
+    it.sd = density ? B.scale_f : 1.f;
+    it.box_scale = B.scale;
+    return it;
+}
+
+// Rows of a (tile + halo) box walked by the warps of a CTA: a lane takes x
+// unit qx = lq (+ multiples of nql) of every row it visits; rows advance by
+// a fixed (y, z) step, so no index is divided in the loop. fn(lz, ly, gz, gy, qx)
+// receives the row's box coordinates and its wrapped grid coordinates.
+// a / b for 0 <= a < 2^21 and b >= 1, exactly, through a float reciprocal:
+// (a + 1/2) / b lies at least 1/(2b) from the nearest integer, while the
+// rounding of the reciprocal and the product moves it by at most about
+// (a/b) 2^-22 < 1/(2b).
+__device__ __forceinline__ int small_div(int a, int b) { return (int)(((float)a + 0.5f) * __frcp_rn((float)b)); }
+
+// Columns of a (tile + halo) box walked by the threads of a CTA: a column is
+// one x unit (quad or value) qx of one y row ly; each thread takes one column
+// and steps through the z planes (several planes at a time when the CTA has
+// threads for more than one plane's columns), so the loop carries only a
+// plane index. fn(lz, ly, gz, gy, qx) receives the box coordinates and the
+// wrapped grid coordinates. Boxes with more columns than threads take the
+// generic walk (one division per value).
+template <typename Fn>
+__device__ __forceinline__ void box_cols(const PairItem &it, int bz, int by, int nq, Fn fn)
+{
+    const int C = by * nq, T = blockDim.x, t = threadIdx.x;
+    if (C <= T) {
+        const int P = small_div(T, C);
+        const int pz = small_div(t, C);
+        if (pz >= P)
+            return;
+        const int c = t - pz * C;
+        const int ly = small_div(c, nq), qx = c - ly * nq;
+        const int gy = wrap1(it.sy - kHaloYZ + ly, it.n);
+        int gz = wrap1(it.sz - kHaloYZ + pz, it.n);
+        for (int lz = pz; lz < bz; lz += P) {
+            fn(lz, ly, gz, gy, qx);
+            gz += P;
+            gz -= gz >= it.n ? it.n : 0;
+        }
+    } else {
+        for (int q = t; q < C * bz; q += T) {
+            const int lz = small_div(q, C), c = q - lz * C;
+            const int ly = small_div(c, nq), qx = c - ly * nq;
+            fn(lz, ly, wrap1(it.sz - kHaloYZ + lz, it.n), wrap1(it.sy - kHaloYZ + ly, it.n), qx);
+        }
+    }
+}
+
+// The same over a box of bz x by rows starting 2 cells below the tile in y
+// and z (the A box and the U box both do).
+template <typename Fn>
+__device__ __forceinline__ void box_rows(const PairItem &it, int bz, int by, int nq, int lane, int wid, int nw,
+                                         Fn fn)
+{
+    const int nql = nq <= 32 ? nq : 32;
+    const int rpw = small_div(32, nql);
+    const int lr = small_div(lane, nql), lq = lane - lr * nql;
+    if (lr >= rpw)
+        return;
+    const int rstep = nw * rpw;
+    const int r0 = wid * rpw + lr;
+    int lz = small_div(r0, by), ly = r0 - lz * by;
+    const int dz = small_div(rstep, by), dy = rstep - dz * by;
+    while (lz < bz) {
+        const int gz = wrap1(it.sz - kHaloYZ + lz, it.n), gy = wrap1(it.sy - kHaloYZ + ly, it.n);
+        for (int qx = lq; qx < nq; qx += nql)
+            fn(lz, ly, gz, gy, qx);
+        ly += dy;
+        lz += dz;
+        if (ly >= by) {
+            ly -= by;
+            ++lz;
+        }
+    }
+}
+
+template <typename Fn>
+__device__ __forceinline__ void pair_rows(const PairItem &it, int nq, int lane, int wid, int nw, Fn fn)
+{
+    box_rows(it, it.bz, it.by, nq, lane, wid, nw, fn);
+}
+// Copies the velocity box of an item's lattice into the U buffer (value i
+// of a row is x = sx - 2 + i, rows from y and z = tile start - 2)
+// asynchronously with cp.async, waited for before the next node loop. When
+// n, the tile start and edge are multiples of 4 and the lattice is 16-byte
+// aligned, the ex values x = sx .. sx + ex - 1 of every row move as 16-byte
+// quads and the two values at each end as 8-byte pairs (two column walks,
+// so no thread branches per copy); otherwise single values.
+__device__ __forceinline__ void pair_stage(const PairItem &it, const float *__restrict__ u, unsigned sU)
+{
+    const long long n3 = (long long)it.n * it.n * it.n;
+    const float *ud = u + it.grid_off + it.d * n3;
+    const bool vec = ((it.sx | it.n | it.ex) & 3) == 0 && ((reinterpret_cast<uintptr_t>(ud)) & 15) == 0;
+    const int n = it.n, bzu = it.ez + 4, byu = it.ey + 4;
+    if (vec) {
+        box_cols(it, bzu, byu, it.ex >> 2, [&](int lz, int ly, int gz, int gy, int qx) {
+            cp_async16(sU + 4u * (unsigned)(lz * it.ppu + ly * it.pxu + 2 + 4 * qx),
+                       ud + (gz * n + gy) * n + it.sx + 4 * qx);
+        });
+        box_cols(it, bzu, byu, 2, [&](int lz, int ly, int gz, int gy, int e) {
+            cp_async8(sU + 4u * (unsigned)(lz * it.ppu + ly * it.pxu + (e ? it.ex + 2 : 0)),
+                      ud + (gz * n + gy) * n + wrap1(e ? it.sx + it.ex : it.sx - 2, n));
+        });
+    } else {
+        box_cols(it, bzu, byu, it.ex + 4, [&](int lz, int ly, int gz, int gy, int qx) {
+            cp_async4(sU + 4u * (unsigned)(lz * it.ppu + ly * it.pxu + qx),
+                      ud + (gz * n + gy) * n + wrap1(it.sx - 2 + qx, n));
+        });
+    }
+}
+
+// sum |F_d| over an item's own nodes, one partial per warp into s_part
+// The first own unit of this thread in an item (node id, binning record,
+// F_d), loaded ahead of the item's node loop.
+struct PairUnit {
+    int node;
+    float4 rec;
+    float f;
+};
+
+// sum |F_d| over an item's own nodes, one partial per warp into s_part; the
+// first unit of this thread is returned for the item's node loop.
+__device__ __forceinline__ PairUnit pair_gsum(const PairItem &it, const DevWork &w, const float *__restrict__ F,
+                                              long long N, float *s_part, int lane, int wid)
+{
+    const int beg = w.own_off[(long long)it.tile * kOwnSub3], end = w.own_off[(long long)(it.tile + 1) * kOwnSub3];
+    PairUnit u0{0, make_float4(0.f, 0.f, 0.f, 0.f), 0.f};
+    int q = beg + (int)threadIdx.x;
+    if (q < end) {
+        u0.node = w.own_nodes[q];
+        u0.rec = w.own_rec[q];
+        u0.f = F[it.d * N + u0.node];
+    }
+    float gs = fabsf(u0.f);
+    for (q += blockDim.x; q < end; q += blockDim.x)
+        gs += fabsf(F[it.d * N + w.own_nodes[q]]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        gs += __shfl_down_sync(0xffffffffu, gs, o);
+    if (lane == 0)
+        s_part[wid] = gs;
+    return u0;
+}
+
+// Fixed-point scale of a (tile, lattice) accumulator: the largest power of
+// two that keeps wmax * sum_k |g_k| (wmax = 1/8 for Peskin, sd the density
+// factor) below the int32 range, from the per-warp partial sums of |F_d|.
+// Every thread computes the same value.
+__device__ __forceinline__ float halo_scale(const float *s_part, int nw, float sd)
+{
+    float tot = 0.f;
+    for (int q = 0; q < nw; ++q)
+        tot += s_part[q];
+    const float bound = tot * sd * 0.125f * 1.0001f;
+    float scale = 1.f;
+    if (bound > 0.f && isfinite(bound)) {
+        int e = (int)floorf(log2f(FixedPoint<int>::kRange / bound));
+        e = e > 120 ? 120 : (e < -120 ? -120 : e);
+        scale = exp2f((float)e);
+    }
+    return scale;
+}
+
 template <bool INTERP, bool AB2 = false>
 __global__ void __launch_bounds__(256, 5) spread_halo_kernel(DevBatch b, DevGrid g, DevWork w,
                                                           const float *__restrict__ x,
@@ -820,45 +1097,32 @@ __global__ void __launch_bounds__(256, 5) spread_halo_kernel(DevBatch b, DevGrid
     int *acc = reinterpret_cast<int *>(halo_smem);
     const unsigned sacc = smem_u32(acc);
     __shared__ float s_part[8];
-    __shared__ float s_scale;
     __shared__ long long s_red[8];
-    __shared__ int s_item;
-    __shared__ TileInfo s_ti;
-    __shared__ BoxDev s_B;
+    // the next item, published by thread 0 in slot (k + 1) & 1 during the
+    // flush of item k and read after that flush's barrier (two slots: the
+    // slot of item k is rewritten only during item k + 1's flush)
+    __shared__ int s_item[2];
+    __shared__ TileInfo s_ti[2];
+    __shared__ BoxDev s_B[2];
     const long long N = b.N;
-    const long long n_items = 3 * g.n_tiles;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int i = threadIdx.x; i < halo_ints(g.max_edge); i += blockDim.x)
         acc[i] = 0;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            long long it;
-            // skip tiles without own nodes
-            for (;;) {
-                it = atomicAdd(&w.counters[2], 1);
-                if (it >= n_items)
-                    break;
-                const long long tile = it / 3;
-                if (w.own_off[(tile + 1) * kOwnSub3] > w.own_off[tile * kOwnSub3])
-                    break;
-            }
-            s_item = it < n_items ? (int)it : -1;
-            if (it < n_items) {
-                s_ti = decode_tile(g, it / 3);
-                s_B = g.boxes[s_ti.box];
-            }
-        }
-        __syncthreads();
-        const int item = s_item;
-        if (item < 0)
+    if (threadIdx.x == 0)
+        staged_next(g, w, s_item[0], s_ti[0], s_B[0]);
+    __syncthreads();
+    for (int slot = 0;; slot ^= 1) {
+        if (s_item[slot] < 0)
             break;
-        const int tile = item / 3, d = item - 3 * (item / 3);
-        const int ex = s_ti.edge[0], ey = s_ti.edge[1], ez = s_ti.edge[2];
-        const int sx = s_ti.start[0], sy = s_ti.start[1], sz = s_ti.start[2];
-        const int bx = ex + 2 * kHaloX, by = ey + 2 * kHaloYZ, bz = ez + 2 * kHaloYZ;
+        // item fields for the node loop, from the shared slot (it stays
+        // valid until the next item's flush; the flush re-reads it)
+        const int tile = s_item[slot] / 3, d = s_item[slot] - 3 * tile;
+        const int sx = s_ti[slot].start[0], sy = s_ti[slot].start[1], sz = s_ti[slot].start[2];
+        const int bx = s_ti[slot].edge[0] + 2 * kHaloX, by = s_ti[slot].edge[1] + 2 * kHaloYZ,
+                  bz = s_ti[slot].edge[2] + 2 * kHaloYZ;
         const int px = halo_px(bx), pp = halo_pp(by, px);
-        const int n = s_B.n;
-        const float sd = density ? s_B.scale_f : 1.f;
+        const int n = s_B[slot].n;
+        const float sd = density ? s_B[slot].scale_f : 1.f;
         const int beg = w.own_off[(long long)tile * kOwnSub3], end = w.own_off[(long long)(tile + 1) * kOwnSub3];
         // fixed-point scale from sum |F_d| over the own nodes
         float gs = 0.f;
@@ -870,21 +1134,7 @@ __global__ void __launch_bounds__(256, 5) spread_halo_kernel(DevBatch b, DevGrid
         if (lane == 0)
             s_part[wid] = gs;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            float tot = 0.f;
-            for (int q = 0; q < nw; ++q)
-                tot += s_part[q];
-            const float bound = tot * sd * 0.125f * 1.0001f;
-            float sc = 1.f;
-            if (bound > 0.f && isfinite(bound)) {
-                int e = (int)floorf(log2f(FixedPoint<int>::kRange / bound));
-                e = e > 120 ? 120 : (e < -120 ? -120 : e);
-                sc = exp2f((float)e);
-            }
-            s_scale = sc;
-        }
-        __syncthreads();
-        const float gsc = sd * s_scale;
+        const float gsc = sd * halo_scale(s_part, nw, sd);
         for (int q = beg + threadIdx.x; q < end; q += blockDim.x) {
             const int node = w.own_nodes[q];
             const float4 rec = w.own_rec[q];   // written by the binning
@@ -921,7 +1171,7 @@ __global__ void __launch_bounds__(256, 5) spread_halo_kernel(DevBatch b, DevGrid
                 // grid indices of the stencil (the buffer origin is the tile
                 // start minus the halo); per z plane the 16 gathers are issued
                 // before that plane's shared-memory reductions
-                const float *ud = u + s_B.grid_off + (long long)d * n * n * n;
+                const float *ud = u + s_B[slot].grid_off + (long long)d * n * n * n;
                 int gx[4], gy[4], gz[4];
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
@@ -981,82 +1231,309 @@ __global__ void __launch_bounds__(256, 5) spread_halo_kernel(DevBatch b, DevGrid
             }
         }
         __syncthreads();
-        // flush. Each warp takes groups of whole rows, a lane one quad (or one
-        // value when rows are not 16-byte aligned) at a fixed x; rows advance
-        // by a fixed (y, z) step, so no index is divided in the loop. Quads
-        // lie inside [0, n) after the periodic wrap when n and the tile start
-        // are multiples of 4.
-        const long long n3 = (long long)n * n * n;
-        float *fd = f + s_B.grid_off + d * n3;
-        const bool vec = ((sx | n | bx) & 3) == 0 && ((reinterpret_cast<uintptr_t>(fd)) & 15) == 0;
-        const float inv = 1.f / s_scale;
-        const int per = vec ? 4 : 1;
-        const int nq = bx / per;                        // quads (or values) per row
-        const int nql = nq <= 32 ? nq : 32;             // lanes per row
-        const int rpw = 32 / nql;                       // rows per warp step
-        const int lr = lane / nql, lq = lane - lr * nql;
-        long long qsum = 0;
-        unsigned touched = 0;
-        if (lr < rpw) {
-            const int rstep = nw * rpw;
-            int r0 = wid * rpw + lr;
-            int lz = r0 / by, ly = r0 - lz * by;
-            const int dz = rstep / by, dy = rstep - dz * by;
-            for (; lz < bz;) {
-                const int gz = wrap_near(sz - kHaloYZ + lz, n), gy = wrap_near(sy - kHaloYZ + ly, n);
-                float *dst = fd + ((long long)gz * n + gy) * n;
-                int *src = acc + lz * pp + ly * px;
-                const bool row_in =
-                    (unsigned)(lz - kHaloYZ) < (unsigned)ez && (unsigned)(ly - kHaloYZ) < (unsigned)ey;
-                if (vec) {
-                    const int x0 = lq << 2;
-                    int4 *sp = reinterpret_cast<int4 *>(src + x0);
+        // flush: every non-zero sum is added to the grid with an L2 reduction
+        // (quads of x when rows are 16-byte aligned) and cleared; meanwhile
+        // thread 0 fetches the next item
+        if (threadIdx.x == 0)
+            staged_next(g, w, s_item[slot ^ 1], s_ti[slot ^ 1], s_B[slot ^ 1]);
+        const PairItem cur = pair_item(s_item[slot], s_ti[slot], s_B[slot], density);
+        const float scale = halo_scale(s_part, nw, cur.sd);   // the node loop's scale, recomputed
+        {
+            const long long n3 = (long long)n * n * n;
+            float *fd = f + cur.grid_off + d * n3;
+            const bool vec = ((sx | n | bx) & 3) == 0 && ((reinterpret_cast<uintptr_t>(fd)) & 15) == 0;
+            const float inv = 1.f / scale;
+            long long qsum = 0;
+            unsigned touched = 0;
+            if (vec) {
+                pair_rows(cur, bx >> 2, lane, wid, nw, [&](int lz, int ly, int gz, int gy, int qx) {
+                    int4 *sp = reinterpret_cast<int4 *>(acc + lz * pp + ly * px + 4 * qx);
                     const int4 qv = *sp;
                     if ((qv.x | qv.y | qv.z | qv.w) != 0) {
                         *sp = make_int4(0, 0, 0, 0);
-                        red_add_v4(dst + wrap_near(sx - kHaloX + x0, n), (float)qv.x * inv, (float)qv.y * inv,
-                                   (float)qv.z * inv, (float)qv.w * inv);
+                        const int x0 = 4 * qx;
+                        red_add_v4(fd + (gz * n + gy) * n + wrap1(sx - kHaloX + x0, n), (float)qv.x * inv,
+                                   (float)qv.y * inv, (float)qv.z * inv, (float)qv.w * inv);
                         qsum += (long long)qv.x + (long long)qv.y + (long long)qv.z + (long long)qv.w;
-                        if (row_in && (unsigned)(x0 - kHaloX) < (unsigned)ex)
+                        if ((unsigned)(lz - kHaloYZ) < (unsigned)cur.ez && (unsigned)(ly - kHaloYZ) < (unsigned)cur.ey &&
+                            (unsigned)(x0 - kHaloX) < (unsigned)cur.ex)
                             touched += (qv.x != 0) + (qv.y != 0) + (qv.z != 0) + (qv.w != 0);
                     }
-                } else {
-                    for (int qx = lq; qx < bx; qx += nql) {
-                        const int q = src[qx];
-                        if (q != 0) {
-                            src[qx] = 0;
-                            red_add(dst + wrap_near(sx - kHaloX + qx, n), (float)q * inv);
-                            qsum += q;
-                            touched += row_in && (unsigned)(qx - kHaloX) < (unsigned)ex;
-                        }
+                });
+            } else {
+                pair_rows(cur, bx, lane, wid, nw, [&](int lz, int ly, int gz, int gy, int qx) {
+                    int *sp = acc + lz * pp + ly * px + qx;
+                    const int qv = *sp;
+                    if (qv != 0) {
+                        *sp = 0;
+                        red_add(fd + (gz * n + gy) * n + wrap1(sx - kHaloX + qx, n), (float)qv * inv);
+                        qsum += qv;
+                        touched += (unsigned)(lz - kHaloYZ) < (unsigned)cur.ez &&
+                                   (unsigned)(ly - kHaloYZ) < (unsigned)cur.ey && (unsigned)(qx - kHaloX) < (unsigned)cur.ex;
                     }
-                }
-                ly += dy;
-                lz += dz;
-                if (ly >= by) {
-                    ly -= by;
-                    ++lz;
-                }
+                });
             }
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            qsum += __shfl_down_sync(0xffffffffu, qsum, o);
-            touched += __shfl_down_sync(0xffffffffu, touched, o);
-        }
-        if (lane == 0) {
-            s_red[wid] = qsum;
-            status_add(w.status, ST_TOUCHED, touched);
+            for (int o = 16; o > 0; o >>= 1) {
+                qsum += __shfl_down_sync(0xffffffffu, qsum, o);
+                touched += __shfl_down_sync(0xffffffffu, touched, o);
+            }
+            if (lane == 0) {
+                s_red[wid] = qsum;
+                if (touched)
+                    status_add(w.status, ST_TOUCHED, touched);
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            long long v = 0;
+            long long vsum = 0;
             for (int q = 0; q < nw; ++q)
-                v += s_red[q];
-            // exact: |v| < 2^53, inv a power of two
-            w.red_tile[3LL * tile + d] = (double)v * (double)inv / s_B.scale;
+                vsum += s_red[q];
+            // exact: |vsum| < 2^53, 1/scale a power of two
+            w.red_tile[3LL * tile + d] = (double)vsum * (double)(1.f / scale) / cur.box_scale;
         }
-        // the next iteration's barrier orders these reads before s_red is rewritten
+        // s_part and s_red are written again only after the next barriers
+    }
+}
+
+// ---------------------------------- spread + interp, FP32, staged velocity
+// IFEM_SCATTER_ATOMIC, Peskin kernel, with the interpolation of the same
+// step fused (Algorithm steps 2 and 4 use the same stencil weights of the
+// same positions). Work item = (tile, lattice) over the tiles with own
+// nodes (own_tiles_kernel), taken from a global counter; thread 0 fetches
+// the next item during the node loop. Two shared buffers per CTA: U, the
+// velocity values the item's stencils read (2 cells around the tile), and A,
+// the spread accumulator over the tile plus the halo of spread_halo_kernel
+// (int32 fixed point, scale from the bound sum_k |g_k| / 8 over the tile's
+// own nodes). Per item:
+//   1. node loop, one (node, lattice) unit per thread: the Peskin weights
+//      of the unit; interpolation from U (64 shared-memory loads at
+//      immediate offsets, v_d = sum phi u_d in z-y-x order), then the 64
+//      contributions added to A with shared-memory reductions;
+//   2. the next item's velocity box is copied into U (cp.async) and its
+//      scale bound summed (which also loads each thread's first unit of the
+//      next item) while A is flushed: every non-zero value is added to the
+//      grid with an L2 reduction (halos of neighbouring tiles combine there)
+//      and cleared.
+// CTAs are small (kStagedThreads): an item has a few hundred units, and the
+// last round of the node loop leaves threads idle at the barrier; with
+// fewer threads per CTA that round is a smaller share of the item.
+// AB2 = true also writes the position update of Eq. Bashforth_eqn from each
+// interpolated velocity, out of place.
+template <bool AB2>
+__global__ void __launch_bounds__(kStagedThreads, 3) transfer_staged_kernel(DevBatch b, DevGrid g, DevWork w,
+                                                                     const float *__restrict__ x,
+                                                                     const float *__restrict__ F,
+                                                                     float *__restrict__ f, int density,
+                                                                     const float *__restrict__ u,
+                                                                     float *__restrict__ v,
+                                                                     const float *__restrict__ vp,
+                                                                     float *__restrict__ xn, float dt)
+{
+    extern __shared__ __align__(16) unsigned char pair_smem[];
+    __shared__ float s_part[kStagedThreads / 32];
+    __shared__ long long s_red[kStagedThreads / 32];
+    // the next item, published by thread 0 in slot (k + 1) & 1 during the
+    // node loop of item k and read after that loop's barrier (two slots: the
+    // slot of item k is rewritten only during item k + 1's node loop)
+    __shared__ int s_item[2];
+    __shared__ TileInfo s_ti[2];
+    __shared__ BoxDev s_B[2];
+    const int ubytes = pair_u_bytes(g.max_edge), buf = pair_buf_bytes(g.max_edge);
+    const float *U = reinterpret_cast<const float *>(pair_smem + 8);
+    int *A = reinterpret_cast<int *>(pair_smem + ubytes);
+    const unsigned sU = smem_u32(pair_smem) + 8u, sA = smem_u32(pair_smem) + (unsigned)ubytes;
+    const long long N = b.N;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < buf / 16; i += blockDim.x)
+        reinterpret_cast<int4 *>(A)[i] = make_int4(0, 0, 0, 0);
+    if (threadIdx.x == 0)
+        staged_next(g, w, s_item[0], s_ti[0], s_B[0]);
+    __syncthreads();
+    if (s_item[0] < 0)
+        return;
+    PairUnit u0;
+    {
+        const PairItem first = pair_item(s_item[0], s_ti[0], s_B[0], density);
+        pair_stage(first, u, sU);
+        u0 = pair_gsum(first, w, F, N, s_part, lane, wid);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int slot = 0;; slot ^= 1) {
+        const PairItem cur = pair_item(s_item[slot], s_ti[slot], s_B[slot], density);
+        // fixed-point scale of this item from the partial sums of |F_d|
+        float scale = 1.f;
+        {
+            float tot = 0.f;
+            for (int q = 0; q < nw; ++q)
+                tot += s_part[q];
+            const float bound = tot * cur.sd * 0.125f * 1.0001f;
+            if (bound > 0.f && isfinite(bound)) {
+                int e = (int)floorf(log2f(FixedPoint<int>::kRange / bound));
+                e = e > 120 ? 120 : (e < -120 ? -120 : e);
+                scale = exp2f((float)e);
+            }
+        }
+        const float gsc = cur.sd * scale;
+        if (threadIdx.x == 0)
+            staged_next(g, w, s_item[slot ^ 1], s_ti[slot ^ 1], s_B[slot ^ 1]);
+        const int d = cur.d;
+        const int beg = w.own_off[(long long)cur.tile * kOwnSub3];
+        const int end = w.own_off[(long long)(cur.tile + 1) * kOwnSub3];
+        const int px = cur.px, pp = cur.pp;
+        // 1. node loop: one (node, lattice) unit per thread; the first unit
+        // was loaded with the scale sum
+        PairUnit un = u0;
+        for (int q = beg + (int)threadIdx.x; q < end;) {
+            const int node = un.node;
+            const float4 rec = un.rec;   // written by the binning
+            const float gq = un.f * gsc;
+            q += blockDim.x;
+            if (q < end) {
+                un.node = w.own_nodes[q];
+                un.rec = w.own_rec[q];
+                un.f = F[d * N + un.node];
+            }
+            const unsigned pk = __float_as_uint(rec.w);
+            const float fr[3] = {rec.x, rec.y, rec.z};
+            float ph[3][4];
+            int l0[3];
+            bool inside = true;
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                // lattice d sits at the cell coordinate, the other two half a
+                // cell lower: s = t - 1/2 has floor(t) - 1 and fraction r + 1/2
+                // below r = 1/2, so the stencil starts 2 (not 1) cells below
+                const int c = (int)((pk >> (8 * ax)) & 255u);   // cell within the tile
+                int sh = -1;
+                float r = fr[ax];
+                if (ax != d) {
+                    const bool low = r < 0.5f;
+                    r = low ? r + 0.5f : r - 0.5f;
+                    sh = low ? -2 : -1;
+                }
+                peskin_frac(r, ph[ax]);
+                l0[ax] = c + (ax == 0 ? kHaloX : kHaloYZ) + sh;
+                // inside both boxes: in x within [2, ex + 2] of A (U starts
+                // 2 cells later), in y and z within [0, e]
+                const int lo = ax == 0 ? 2 : 0;
+                const int hi = ax == 0 ? cur.ex + 2 : (ax == 1 ? cur.ey : cur.ez);
+                inside = inside && (unsigned)(l0[ax] - lo) <= (unsigned)(hi - lo);
+            }
+            if (!inside) {   // a record inconsistent with this tile: never expected
+                status_add(w.status, ST_DOMAIN, 1);
+                continue;
+            }
+            const int off = l0[2] * pp + l0[1] * px + l0[0];
+            const float *ub = U + (l0[2] * cur.ppu + l0[1] * cur.pxu + (l0[0] - 2));
+            const unsigned ab = sA + 4u * (unsigned)off;
+            // interpolation first (all 64 loads can be in flight), then the
+            // 64 fixed-point reductions; the reductions carry no compiler
+            // memory clobber, so they do not hold back the loads of the next
+            // unit (the barrier after the loop orders them)
+            float out = 0.f;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float accz = 0.f;
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb) {
+                    const float *row = ub + c * cur.ppu + bb * cur.pxu;
+                    float accy = ph[0][0] * row[0];
+#pragma unroll
+                    for (int a = 1; a < 4; ++a)
+                        accy += ph[0][a] * row[a];
+                    accz += ph[1][bb] * accy;
+                }
+                out += ph[2][c] * accz;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float wz = ph[2][c] * gq;
+#pragma unroll
+                for (int bb = 0; bb < 4; ++bb) {
+                    const float wyz = ph[1][bb] * wz;
+                    const unsigned arow = ab + 4u * (unsigned)(c * pp + bb * px);
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+                        red_shared_add_nc(arow + 4u * a, __float2int_rn(ph[0][a] * wyz));
+                }
+            }
+            v[d * N + node] = out;
+            if constexpr (AB2) {
+                const long long i = d * N + node;
+                xn[i] = ab2_value(x[i], out, vp[i], dt);
+            }
+        }
+        asm volatile("" ::: "memory");   // the reductions above stay before the barrier
+        __syncthreads();   // A complete, U free, the next item published
+
+        // 2. next item's velocities and scale bound; flush of A
+        const int next = s_item[slot ^ 1];
+        if (next >= 0) {
+            const PairItem nxt = pair_item(next, s_ti[slot ^ 1], s_B[slot ^ 1], density);
+            pair_stage(nxt, u, sU);
+            u0 = pair_gsum(nxt, w, F, N, s_part, lane, wid);
+        }
+        {
+            const long long n3 = (long long)cur.n * cur.n * cur.n;
+            float *fd = f + cur.grid_off + d * n3;
+            const bool vec = ((cur.sx | cur.n | cur.bx) & 3) == 0 && ((reinterpret_cast<uintptr_t>(fd)) & 15) == 0;
+            const float inv = 1.f / scale;
+            const int n = cur.n;
+            long long qsum = 0;
+            unsigned touched = 0;
+            if (vec) {
+                box_cols(cur, cur.bz, cur.by, cur.bx >> 2, [&](int lz, int ly, int gz, int gy, int qx) {
+                    int4 *sp = reinterpret_cast<int4 *>(A + lz * pp + ly * px + 4 * qx);
+                    const int4 qv = *sp;
+                    if ((qv.x | qv.y | qv.z | qv.w) != 0) {
+                        *sp = make_int4(0, 0, 0, 0);
+                        const int x0 = 4 * qx;
+                        red_add_v4(fd + (gz * n + gy) * n + wrap1(cur.sx - kHaloX + x0, n), (float)qv.x * inv,
+                                   (float)qv.y * inv, (float)qv.z * inv, (float)qv.w * inv);
+                        qsum += (long long)qv.x + (long long)qv.y + (long long)qv.z + (long long)qv.w;
+                        if ((unsigned)(lz - kHaloYZ) < (unsigned)cur.ez && (unsigned)(ly - kHaloYZ) < (unsigned)cur.ey &&
+                            (unsigned)(x0 - kHaloX) < (unsigned)cur.ex)
+                            touched += (qv.x != 0) + (qv.y != 0) + (qv.z != 0) + (qv.w != 0);
+                    }
+                });
+            } else {
+                box_cols(cur, cur.bz, cur.by, cur.bx, [&](int lz, int ly, int gz, int gy, int qx) {
+                    int *sp = A + lz * pp + ly * px + qx;
+                    const int qv = *sp;
+                    if (qv != 0) {
+                        *sp = 0;
+                        red_add(fd + (gz * n + gy) * n + wrap1(cur.sx - kHaloX + qx, n), (float)qv * inv);
+                        qsum += qv;
+                        touched += (unsigned)(lz - kHaloYZ) < (unsigned)cur.ez &&
+                                   (unsigned)(ly - kHaloYZ) < (unsigned)cur.ey && (unsigned)(qx - kHaloX) < (unsigned)cur.ex;
+                    }
+                });
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                qsum += __shfl_down_sync(0xffffffffu, qsum, o);
+                touched += __shfl_down_sync(0xffffffffu, touched, o);
+            }
+            if (lane == 0) {
+                s_red[wid] = qsum;
+                if (touched)
+                    status_add(w.status, ST_TOUCHED, touched);
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();   // U holds the next box, A is clear, s_part and s_red are written
+        if (threadIdx.x == 0) {
+            long long vsum = 0;
+            for (int q = 0; q < nw; ++q)
+                vsum += s_red[q];
+            // exact: |vsum| < 2^53, 1/scale a power of two
+            w.red_tile[3LL * cur.tile + d] = (double)vsum * (double)(1.f / scale) / cur.box_scale;
+        }
+        if (next < 0)
+            break;
+        // s_red and s_part are written again only after the next node loop's barrier
     }
 }
 
