@@ -817,6 +817,7 @@ static int do_spread_interp(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void 
     a.vp = vp;
     a.xn = xn;
     a.dt = dt;
+    a.binned = 1;   // every caller bins on this stream just before
     return launch_rc(ctx, launch_spread_f32(a), "spread + interpolate");
 }
 

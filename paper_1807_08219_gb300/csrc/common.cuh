@@ -348,6 +348,8 @@ struct TransferArgs {
     int acc64;        // FP32 spread: 64-bit (1) or 32-bit (0) fixed-point accumulators
     int halo;         // FP32 Peskin spread with halo scatter (IFEM_SCATTER_ATOMIC): 1; 2 with the
                       // velocity box staged in shared memory when interpolation is fused
+    int binned;       // the binning of this step ran just before on the same stream (own tiles
+                      // listed, work counter and per-tile sums cleared)
     int use_wtab;     // FP64 Peskin interpolation: read the stencils the binning of x tabulated
     const void *vp;   // fused position update (halo spread + interpolation only):
     void *xn;         //   xn = x + dt (3/2 v - 1/2 vp) when xn is not null

@@ -110,13 +110,18 @@ cudaError_t spread_impl(const TransferArgs &a)
 {
     const DevBatch &b = a.b;
     cudaStream_t s = a.stream;
-    cudaMemsetAsync(a.w.red_tile, 0, sizeof(double) * 3 * a.g.n_tiles, s);
+    // the fused halo transfer right after its binning: own_tiles_kernel cleared
+    // the per-tile sums and the binning the work counter
+    const bool cleared = a.binned && a.halo && a.u != nullptr && a.v != nullptr;
+    if (!cleared)
+        cudaMemsetAsync(a.w.red_tile, 0, sizeof(double) * 3 * a.g.n_tiles, s);
     IFEM_LAUNCH_CHECK();
     if (b.n_inst == 0 || b.N == 0)
         return cudaSuccess;
     if constexpr (std::is_same<real, float>::value) {
         const int E = a.g.max_edge;
-        cudaMemsetAsync(a.w.counters + 2, 0, sizeof(int), s);
+        if (!cleared)
+            cudaMemsetAsync(a.w.counters + 2, 0, sizeof(int), s);
         if (a.halo) {
             // with u and v given, interpolation is fused into the spread, and
             // with xn also the position update

@@ -809,11 +809,22 @@ __host__ __device__ inline int halo_ints(int E)
 // xn_d = x_d + dt (3/2 v_d - 1/2 vp_d), rounded as in ab2_kernel.
 // Tiles with own nodes, compacted (FP32 halo path): the fused transfer
 // kernel takes its (tile, lattice) items from this list, so no CTA walks
-// empty tiles. counters[3] receives the number of listed tiles.
+// empty tiles; counters[3] receives the number of listed tiles. The list
+// keeps roughly the tile order, so items running at the same time are
+// spatial neighbours whose velocity rows and grid lines share L2 (listing
+// the largest tiles first measured slower). The per-tile FP64 sums of the
+// spread are cleared here for every tile (the transfer writes them for the
+// listed tiles only).
 static __global__ void own_tiles_kernel(long long n_tiles, DevWork w)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool has = t < n_tiles && w.own_off[(t + 1) * kOwnSub3] > w.own_off[t * kOwnSub3];
+    bool has = false;
+    if (t < n_tiles) {
+        has = w.own_off[(t + 1) * kOwnSub3] > w.own_off[t * kOwnSub3];
+        w.red_tile[3 * t] = 0.0;
+        w.red_tile[3 * t + 1] = 0.0;
+        w.red_tile[3 * t + 2] = 0.0;
+    }
     const unsigned m = __ballot_sync(0xffffffffu, has);
     const int lane = threadIdx.x & 31;
     int base = 0;
@@ -839,7 +850,7 @@ __device__ __forceinline__ void cp_async16(unsigned dst, const void *src)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Next (tile, lattice) item of the staged transfer kernel (thread 0): items
+// Next (tile, lattice) item of the fused transfer kernels (thread 0): items
 // are the three lattices of each listed tile, in list order.
 __device__ __forceinline__ void staged_next(const DevGrid &g, const DevWork &w, int &item, TileInfo &ti,
                                             BoxDev &B)
