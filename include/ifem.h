@@ -413,8 +413,11 @@ int ifem_step_coupling_ab2(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *
  * (cudaHostAlloc); pageable memory works outside graph capture but copies
  * without overlap. With IFEM_FP32, IFEM_SCATTER_ATOMIC and a batch of two or
  * more particles the positions arrive in two halves (by particle) and each
- * half's element forces start as soon as it has landed; v goes back beside
- * the sums of v and the boxes. Results equal those of copying x in, calling
+ * half's element forces start as soon as it has landed; with the Peskin
+ * kernel the fused spreading and interpolation then run as one launch per
+ * lattice, and row d of v goes back to the host as soon as lattice d is done
+ * (rows 0 and 1 beside the later lattices, row 2 beside the sums of v and the
+ * boxes). Results equal those of copying x in, calling
  * ifem_step_coupling and copying v and red out. Returns IFEM_ERR_ARG for null
  * host arrays (N > 0) or red_host without red. */
 int ifem_step_coupling_host(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x_host, void *x,

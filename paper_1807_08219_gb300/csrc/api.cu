@@ -751,6 +751,7 @@ static TransferArgs transfer_args(ifem_ctx ctx, ifem_batch b, const void *x, con
     a.n_sm = ctx->n_sm;
     a.acc64 = ctx->acc64;
     a.halo = use_halo(ctx) ? (ctx->staged ? 2 : 1) : 0;
+    a.lattice = -1;
     a.stream = (cudaStream_t)stream;
     return a;
 }
@@ -806,7 +807,7 @@ static int do_spread(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
 // velocities it gathers (xn = x + dt (3/2 v - 1/2 vp)).
 static int do_spread_interp(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *F, const void *u,
                             void *f, void *v, int flags, void *stream, const void *vp = nullptr,
-                            void *xn = nullptr, double dt = 0.0)
+                            void *xn = nullptr, double dt = 0.0, int lattice = -1)
 {
     if (flags & IFEM_SPREAD_OVERWRITE) {
         cudaError_t e = cudaMemsetAsync(f, 0, (size_t)g->total * real_size(ctx), (cudaStream_t)stream);
@@ -818,6 +819,7 @@ static int do_spread_interp(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void 
     a.xn = xn;
     a.dt = dt;
     a.binned = 1;   // every caller bins on this stream just before
+    a.lattice = lattice;
     return launch_rc(ctx, launch_spread_f32(a), "spread + interpolate");
 }
 
@@ -1224,7 +1226,25 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
     }
     if ((e = cudaStreamWaitEvent(s, ctx->fork[1], 0)) != cudaSuccess)
         return launch_rc(ctx, e, "step_coupling join");
-    if (fused) {
+    // with host arrays and the staged transfer, one launch per lattice: row d
+    // of v goes back to the host on aux1 as soon as lattice d's launch ends,
+    // beside the later lattices
+    const bool v_rows = fused && io && ctx->staged && node_bytes > 0 && !(flags & IFEM_SPREAD_OVERWRITE);
+    if (v_rows) {
+        const size_t row = node_bytes / 3;
+        for (int d = 0; d < 3; ++d) {
+            if ((rc = do_spread_interp(ctx, b, g, x, F, u, f, v, flags, stream, vp, xn, dt, d)) != IFEM_OK)
+                return rc;
+            if ((e = cudaEventRecord(ctx->fork[d == 2 ? 7 : 2 + d], s)) == cudaSuccess &&
+                (e = cudaStreamWaitEvent(ctx->aux[1], ctx->fork[d == 2 ? 7 : 2 + d], 0)) == cudaSuccess)
+                e = cudaMemcpyAsync((char *)io->v_host + d * row, (const char *)v + d * row, row,
+                                    cudaMemcpyDeviceToHost, ctx->aux[1]);
+            if (e != cudaSuccess)
+                return launch_rc(ctx, e, "step_coupling_host: copy out");
+        }
+        if ((e = cudaEventRecord(ctx->fork[8], ctx->aux[1])) != cudaSuccess)
+            return launch_rc(ctx, e, "step_coupling_host: copy out");
+    } else if (fused) {
         if ((rc = do_spread_interp(ctx, b, g, x, F, u, f, v, flags, stream, vp, xn, dt)) != IFEM_OK)
             return rc;
     } else {
@@ -1233,7 +1253,7 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
         if ((e = cudaStreamWaitEvent(s, ctx->fork[3], 0)) != cudaSuccess)
             return launch_rc(ctx, e, "step_coupling join");
     }
-    const bool v_out = io && node_bytes > 0;
+    const bool v_out = io && node_bytes > 0 && !v_rows;
     if (v_out) {
         // v is complete here: copy it back beside the remaining sums
         if ((e = cudaEventRecord(ctx->fork[7], s)) == cudaSuccess &&
@@ -1253,7 +1273,7 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
         (e = cudaMemcpyAsync(io->red_host, red, io->red_n * sizeof(double), cudaMemcpyDeviceToHost, s)) !=
             cudaSuccess)
         return launch_rc(ctx, e, "step_coupling_host: copy out");
-    if (v_out && (e = cudaStreamWaitEvent(s, ctx->fork[8], 0)) != cudaSuccess)
+    if ((v_out || v_rows) && (e = cudaStreamWaitEvent(s, ctx->fork[8], 0)) != cudaSuccess)
         return launch_rc(ctx, e, "step_coupling_host: join");
     return IFEM_OK;
 }

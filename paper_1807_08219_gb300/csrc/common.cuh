@@ -126,7 +126,7 @@ struct DevWork {
     int *active;        // tiles with candidate pairs
     int *own_tiles;     // tiles with own nodes (FP32 halo path), counters[3] of them
     int *counters;      // [0] n_active, [2] work counter, [3] tiles with own nodes, [4] total pairs,
-                        // [5] total own nodes
+                        // [5] total own nodes, [1] [6] [7] work counters of one-lattice launches
     int *scan_blocks;   // block partial sums for the tile scan
     void *elem_buf;     // per element nodal forces (12 reals per element)
     void *bend_buf;     // per node bending scratch (A, kH, n[3], lap) 6 reals
@@ -350,6 +350,7 @@ struct TransferArgs {
                       // velocity box staged in shared memory when interpolation is fused
     int binned;       // the binning of this step ran just before on the same stream (own tiles
                       // listed, work counter and per-tile sums cleared)
+    int lattice;      // staged fused transfer: -1 all three lattices, else that lattice only
     int use_wtab;     // FP64 Peskin interpolation: read the stencils the binning of x tabulated
     const void *vp;   // fused position update (halo spread + interpolation only):
     void *xn;         //   xn = x + dt (3/2 v - 1/2 vp) when xn is not null

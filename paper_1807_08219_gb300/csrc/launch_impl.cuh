@@ -135,7 +135,8 @@ cudaError_t spread_impl(const TransferArgs &a)
                 occ = occ < 1 ? 1 : occ;
                 kp<<<a.n_sm * occ, kStagedThreads, sm, s>>>(b, a.g, a.w, (const float *)a.x, (const float *)a.F,
                                                           (float *)a.f, a.density, (const float *)a.u, (float *)a.v,
-                                                          (const float *)a.vp, (float *)a.xn, (float)a.dt);
+                                                          (const float *)a.vp, (float *)a.xn, (float)a.dt,
+                                                          a.lattice);
                 IFEM_LAUNCH_CHECK();
                 return cudaSuccess;
             }

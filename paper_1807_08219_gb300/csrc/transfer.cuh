@@ -851,17 +851,32 @@ __device__ __forceinline__ void cp_async16(unsigned dst, const void *src)
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Next (tile, lattice) item of the fused transfer kernels (thread 0): items
-// are the three lattices of each listed tile, in list order.
-__device__ __forceinline__ void staged_next(const DevGrid &g, const DevWork &w, int &item, TileInfo &ti,
-                                            BoxDev &B)
+// are the three lattices of each listed tile, in list order (lattice < 0,
+// work counter counters[2]), or lattice d of each listed tile (work
+// counters[1], [6], [7] for d = 0, 1, 2), so that one launch per lattice
+// completes row d of v at its end.
+__device__ __forceinline__ void staged_next(const DevGrid &g, const DevWork &w, int lattice, int &item,
+                                            TileInfo &ti, BoxDev &B)
 {
-    const int n_items = 3 * w.counters[3];
-    const int it = atomicAdd(&w.counters[2], 1);
+    const int n_tiles = w.counters[3];
+    int tile = -1, d = 0;
+    if (lattice < 0) {
+        const int it = atomicAdd(&w.counters[2], 1);
+        if (it < 3 * n_tiles) {
+            const int q = it / 3;
+            tile = w.own_tiles[q];
+            d = it - 3 * q;
+        }
+    } else {
+        const int it = atomicAdd(&w.counters[lattice == 0 ? 1 : (lattice == 1 ? 6 : 7)], 1);
+        if (it < n_tiles) {
+            tile = w.own_tiles[it];
+            d = lattice;
+        }
+    }
     item = -1;
-    if (it < n_items) {
-        const int q = it / 3;
-        const int tile = w.own_tiles[q];
-        item = 3 * tile + (it - 3 * q);
+    if (tile >= 0) {
+        item = 3 * tile + d;
         ti = decode_tile(g, tile);
         B = g.boxes[ti.box];
     }
@@ -1103,6 +1118,7 @@ __global__ void __launch_bounds__(256, 5) spread_halo_kernel(DevBatch b, DevGrid
                                                           float *__restrict__ v, const float *__restrict__ vp,
                                                           float *__restrict__ xn, float dt)
 {
+    const int lattice = -1;   // every lattice in one launch
     static_assert(INTERP || !AB2, "the position update needs the fused interpolation");
     extern __shared__ __align__(16) unsigned char halo_smem[];
     int *acc = reinterpret_cast<int *>(halo_smem);
@@ -1120,7 +1136,7 @@ __global__ void __launch_bounds__(256, 5) spread_halo_kernel(DevBatch b, DevGrid
     for (int i = threadIdx.x; i < halo_ints(g.max_edge); i += blockDim.x)
         acc[i] = 0;
     if (threadIdx.x == 0)
-        staged_next(g, w, s_item[0], s_ti[0], s_B[0]);
+        staged_next(g, w, lattice, s_item[0], s_ti[0], s_B[0]);
     __syncthreads();
     for (int slot = 0;; slot ^= 1) {
         if (s_item[slot] < 0)
@@ -1246,7 +1262,7 @@ __global__ void __launch_bounds__(256, 5) spread_halo_kernel(DevBatch b, DevGrid
         // (quads of x when rows are 16-byte aligned) and cleared; meanwhile
         // thread 0 fetches the next item
         if (threadIdx.x == 0)
-            staged_next(g, w, s_item[slot ^ 1], s_ti[slot ^ 1], s_B[slot ^ 1]);
+            staged_next(g, w, lattice, s_item[slot ^ 1], s_ti[slot ^ 1], s_B[slot ^ 1]);
         const PairItem cur = pair_item(s_item[slot], s_ti[slot], s_B[slot], density);
         const float scale = halo_scale(s_part, nw, cur.sd);   // the node loop's scale, recomputed
         {
@@ -1330,7 +1346,8 @@ __global__ void __launch_bounds__(256, 5) spread_halo_kernel(DevBatch b, DevGrid
 // last round of the node loop leaves threads idle at the barrier; with
 // fewer threads per CTA that round is a smaller share of the item.
 // AB2 = true also writes the position update of Eq. Bashforth_eqn from each
-// interpolated velocity, out of place.
+// interpolated velocity, out of place. lattice >= 0 restricts the launch to
+// that lattice's items (see staged_next).
 template <bool AB2>
 __global__ void __launch_bounds__(kStagedThreads, 3) transfer_staged_kernel(DevBatch b, DevGrid g, DevWork w,
                                                                      const float *__restrict__ x,
@@ -1339,7 +1356,8 @@ __global__ void __launch_bounds__(kStagedThreads, 3) transfer_staged_kernel(DevB
                                                                      const float *__restrict__ u,
                                                                      float *__restrict__ v,
                                                                      const float *__restrict__ vp,
-                                                                     float *__restrict__ xn, float dt)
+                                                                     float *__restrict__ xn, float dt,
+                                                                     int lattice)
 {
     extern __shared__ __align__(16) unsigned char pair_smem[];
     __shared__ float s_part[kStagedThreads / 32];
@@ -1359,7 +1377,7 @@ __global__ void __launch_bounds__(kStagedThreads, 3) transfer_staged_kernel(DevB
     for (int i = threadIdx.x; i < buf / 16; i += blockDim.x)
         reinterpret_cast<int4 *>(A)[i] = make_int4(0, 0, 0, 0);
     if (threadIdx.x == 0)
-        staged_next(g, w, s_item[0], s_ti[0], s_B[0]);
+        staged_next(g, w, lattice, s_item[0], s_ti[0], s_B[0]);
     __syncthreads();
     if (s_item[0] < 0)
         return;
@@ -1388,7 +1406,7 @@ __global__ void __launch_bounds__(kStagedThreads, 3) transfer_staged_kernel(DevB
         }
         const float gsc = cur.sd * scale;
         if (threadIdx.x == 0)
-            staged_next(g, w, s_item[slot ^ 1], s_ti[slot ^ 1], s_B[slot ^ 1]);
+            staged_next(g, w, lattice, s_item[slot ^ 1], s_ti[slot ^ 1], s_B[slot ^ 1]);
         const int d = cur.d;
         const int beg = w.own_off[(long long)cur.tile * kOwnSub3];
         const int end = w.own_off[(long long)(cur.tile + 1) * kOwnSub3];
