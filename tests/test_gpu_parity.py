@@ -221,6 +221,31 @@ def test_fp32_atomic_small_boxes(n, tile):
     assert rel_l2(g["v"], o["v"]) < TOL_V
 
 
+@pytest.mark.parametrize("case", ["C2", "C3", "small"])
+def test_fp32_fused_gather_kernel(case, monkeypatch):
+    """The fused transfer that gathers velocities through L1
+    (spread_halo_kernel<true>, selected by IFEM_TRANSFER=halo when the context
+    is created) against the oracle, as the default staged kernel is."""
+    import dataclasses
+    monkeypatch.setenv("IFEM_TRANSFER", "halo")
+    if case == "small":
+        base = wl("C1")
+        n = 27
+        tm = dataclasses.replace(base.templates[0], X=base.templates[0].X * 0.06 / 0.15)
+        inst = dataclasses.replace(base.instances[0], x_local=base.instances[0].x_local * 0.06 / 0.15,
+                                   origin=np.array([0.93, 0.02, 0.5]))
+        u = np.random.default_rng(n).standard_normal((3, n, n, n))
+        w = dataclasses.replace(base, templates=[tm], instances=[inst], boxes=[W.Box(n, 1.0)], u=[u])
+    else:
+        w = wl(case)
+    w = rounded_workload(w, np.float32)
+    g = run_gpu_step(w, FP32, scatter=1, tile=8 if case == "small" else 0)
+    o = oracle_step(w)
+    assert g["rc"] == 0, g["stats"]
+    eF, ev, ef = rel_l2(g["F"], o["F"]), rel_l2(g["v"], o["v"]), rel_l2(g["f"][0], o["f"][0])
+    assert eF < TOL_F and ev < TOL_V and ef < TOL_GRID, (eF, ev, ef)
+
+
 def test_empty_batch():
     import dataclasses
     w = dataclasses.replace(wl("C1"), instances=[])
