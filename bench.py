@@ -659,9 +659,9 @@ def main():
     if not args.no_cpu:
         cpu = cpu_baseline_parallel(wl)
         cpu["single_thread"] = cpu_baseline_sample(wl)
-    # bin (count, 3 scan, fill, list of tiles with own nodes), forces, spread, interp (or one fused
-    # launch), 2 reductions
-    launches_per_step = 5 + (1 if scatter == I.IFEM_SCATTER_ATOMIC else 0) + 1 + (1 if fused else 2) + 2
+    # bin (halo path: count + rank, scan, placement + list of tiles with own nodes; candidate path:
+    # count, 2 scan, fill), forces, spread, interp (or one fused launch), 2 reductions
+    launches_per_step = (3 if fused else 4) + 1 + (1 if fused else 2) + 2
     if scatter == I.IFEM_SCATTER_DET:
         launches_per_step += 3
     line = {

@@ -624,6 +624,8 @@ extern "C" int ifem_batch_set_origins(ifem_batch b, const double *origins)
     return IFEM_OK;
 }
 
+static int use_halo(ifem_ctx ctx);
+
 // Work buffers for (batch, grid, tile): box/tile tables, per-tile lists.
 static int ws_ensure(ifem_ctx ctx, ifem_batch b, ifem_grid g, int tile)
 {
@@ -672,17 +674,24 @@ static int ws_ensure(ifem_ctx ctx, ifem_batch b, ifem_grid g, int tile)
     CK(alloc((void **)&w.cand_off, sizeof(int) * (nt + 1)));
     CK(alloc((void **)&w.cand_cursor, sizeof(int) * (nt + 1)));
     CK(alloc((void **)&w.cand_nodes, sizeof(int) * (size_t)w.cand_cap));
-    CK(alloc((void **)&w.own_count, sizeof(int) * (no + 1)));
+    CK(alloc((void **)&w.own_count, sizeof(int) * (no + 1 + nt)));
+    w.own_flag = w.own_count + no + 1;
     CK(alloc((void **)&w.own_off, sizeof(int) * (no + 1)));
     CK(alloc((void **)&w.own_cursor, sizeof(int) * (no + 1)));
     CK(alloc((void **)&w.own_nodes, sizeof(int) * (size_t)std::max<long long>(N, 1)));
     CK(alloc((void **)&w.own_rec, sizeof(float4) * (size_t)std::max<long long>(N, 1)));
+    w.node_key = nullptr;
+    w.node_rec = nullptr;
+    if (use_halo(ctx)) {
+        CK(alloc((void **)&w.node_key, sizeof(int2) * (size_t)std::max<long long>(N, 1)));
+        CK(alloc((void **)&w.node_rec, sizeof(float4) * (size_t)std::max<long long>(N, 1)));
+    }
     w.wtab = nullptr;
     if (ctx->cfg.precision == IFEM_FP64 && ctx->cfg.kernel == IFEM_KERNEL_PESKIN4)
         CK(alloc((void **)&w.wtab, sizeof(DetW) * (size_t)std::max<long long>(N, 1)));
     CK(alloc((void **)&w.active, sizeof(int) * (nt + 1)));
     CK(alloc((void **)&w.own_tiles, sizeof(int) * (nt + 1)));
-    CK(alloc((void **)&w.counters, sizeof(int) * 8));
+    CK(alloc((void **)&w.counters, sizeof(int) * kCounters));
     CK(alloc((void **)&w.scan_blocks, sizeof(int) * 2 * (nb + 1)));
     CK(alloc((void **)&w.red_tile, sizeof(double) * 3 * (nt + 1)));
     CK(cudaMemset(w.red_tile, 0, sizeof(double) * 3 * (nt + 1)));
@@ -1154,9 +1163,12 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
     // fork-join over the context's two auxiliary streams (also inside stream
     // capture): forces run beside binning, interpolation (and the position
     // update) beside spreading, and the x/F sums (which need only the forces)
-    // beside the transfers
-    //   s:    bin ----------- wait(forces) spread  wait(interp) wait(sums) sums of v, boxes
-    //   aux0: forces -------/ sums of x, F -----------------------/
+    // beside the transfers. The sums wait for the binning too: started with
+    // the forces' last blocks they slowed the binning's scan, which the
+    // transfer waits for, while the transfer's CTAs take their work from a
+    // counter and absorb them
+    //   s:    bin ----------------------- wait(forces) spread  wait(interp) wait(sums) sums of v, boxes
+    //   aux0: forces --/ wait(bin) sums of x, F -----------------------------/
     //   aux1:       wait(bin) interp [ab2] -------/
     // (with the fused spread + interpolation [+ ab2] the aux1 branch is absent).
     // With host arrays the positions arrive on s in two halves (by particle)
@@ -1164,7 +1176,7 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
     // on aux0 once it has landed; v goes back to the host on aux1 beside the
     // sums of v and the boxes:
     //   s:    copy x[0:h] copy x[h:N] bin ... spread+interp  sums of v, boxes  copy red  wait(copy v)
-    //   aux0:   wait(x[0:h]) forces[0:h] wait(x[h:N]) forces[h:N] sums of x, F
+    //   aux0:   wait(x[0:h]) forces[0:h] wait(x[h:N]) forces[h:N] wait(bin) sums of x, F
     //   aux1:                                           wait(v) copy v ------------------/
     const bool fused = use_halo(ctx) != 0;
     if ((rc = ws_ensure(ctx, b, g, ctx->tile)) != IFEM_OK)
@@ -1203,15 +1215,18 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
     }
     if ((e = cudaEventRecord(ctx->fork[1], ctx->aux[0])) != cudaSuccess)
         return launch_rc(ctx, e, "step_coupling fork");
-    // the x/F sums need only the forces: they run on aux0 beside the transfers
+    if ((rc = do_bin(ctx, b, g, x, stream)) != IFEM_OK)
+        return rc;
+    // the x/F sums, after the forces and the binning, on aux0 beside the transfers
     if (red) {
+        if ((e = cudaEventRecord(ctx->fork[9], s)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(ctx->aux[0], ctx->fork[9], 0)) != cudaSuccess)
+            return launch_rc(ctx, e, "step_coupling fork");
         if ((rc = do_reduce(ctx, b, x, F, v, red, ctx->aux[0], 1)) != IFEM_OK)
             return rc;
         if ((e = cudaEventRecord(ctx->fork[4], ctx->aux[0])) != cudaSuccess)
             return launch_rc(ctx, e, "step_coupling fork");
     }
-    if ((rc = do_bin(ctx, b, g, x, stream)) != IFEM_OK)
-        return rc;
     if (!fused) {
         if ((e = cudaEventRecord(ctx->fork[2], s)) == cudaSuccess)
             e = cudaStreamWaitEvent(ctx->aux[1], ctx->fork[2], 0);

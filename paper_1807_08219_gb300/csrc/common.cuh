@@ -21,6 +21,7 @@ constexpr int kOwnSub3 = kOwnSub * kOwnSub * kOwnSub;
 constexpr int kScanThreads = 512;  // tile-count scan: threads per block
 constexpr int kScanPer = 4;        // and values per thread
 constexpr int kScanBlock = kScanThreads * kScanPer;
+constexpr int kCounters = 16;      // DevWork::counters entries
 // FP32 fused force kernel: 7 floats of shared memory per template node
 constexpr int kMaxCtaSmemBytes = 227 * 1024;   // opt-in dynamic shared memory of one CTA
 constexpr int kFusedMaxSmemBytes = kMaxCtaSmemBytes;
@@ -117,16 +118,21 @@ struct DevWork {
     int *cand_cursor;   // n_tiles
     int *cand_nodes;    // pair list: node id per (tile, node) candidate pair
     long long cand_cap;
-    int *own_count;     // per (tile, 4^3 sub-block): n_tiles * kOwnSub3 + 1
+    int *own_count;     // per (tile, 4^3 sub-block): n_tiles * kOwnSub3 + 1, then own_flag
+    int *own_flag;      // n_tiles (FP32 halo path): 1 where the tile owns a node
     int *own_off;
-    int *own_cursor;
+    int *own_cursor;    // fill cursors; local (per scan block) offsets in the FP32 halo path
     int *own_nodes;     // N entries: nodes grouped by the tile (and sub-block) of their cell
     float4 *own_rec;    // beside own_nodes (FP32 halo path): fractional cell coordinates x, y, z of
                         // the node and, in w, its cell within the tile packed as 8-bit x | y << 8 | z << 16
+    int2 *node_key;     // N entries, by node (FP32 halo path): own-list key (-1: not binned) and
+                        // the node's rank among the nodes of that key
+    float4 *node_rec;   // N entries, by node (FP32 halo path): the own_rec entry of the node
     int *active;        // tiles with candidate pairs
     int *own_tiles;     // tiles with own nodes (FP32 halo path), counters[3] of them
-    int *counters;      // [0] n_active, [2] work counter, [3] tiles with own nodes, [4] total pairs,
-                        // [5] total own nodes, [1] [6] [7] work counters of one-lattice launches
+    int *counters;      // kCounters: [0] n_active, [2] work counter, [3] tiles with own nodes,
+                        // [4] total pairs, [5] total own nodes, [1] [6] [7] work counters of
+                        // one-lattice launches, [8] scan blocks finished
     int *scan_blocks;   // block partial sums for the tile scan
     void *elem_buf;     // per element nodal forces (12 reals per element)
     void *bend_buf;     // per node bending scratch (A, kH, n[3], lap) 6 reals

@@ -26,7 +26,7 @@ struct ifem_ctx_s {
     int staged = 1;   // fused FP32 transfer with the velocity box staged in shared memory
     int tuned = 0;
     cudaStream_t aux[2] = {};   // fork-join streams of ifem_step_coupling
-    static constexpr int kForkEvents = 9;
+    static constexpr int kForkEvents = 10;
     cudaEvent_t fork[kForkEvents] = {};
 };
 

@@ -68,10 +68,12 @@ cudaError_t bin_impl(const TransferArgs &a, int det_sort, int with_cand)
     const DevWork &w = a.w;
     const long long nt = a.g.n_tiles;
     cudaStream_t s = a.stream;
-    cudaMemsetAsync(w.cand_count, 0, sizeof(int) * (nt + 1), s);
     const long long no = nt * kOwnSub3;
-    cudaMemsetAsync(w.own_count, 0, sizeof(int) * (no + 1), s);
-    cudaMemsetAsync(w.counters, 0, sizeof(int) * 8, s);
+    if (with_cand)
+        cudaMemsetAsync(w.cand_count, 0, sizeof(int) * (nt + 1), s);
+    // own counts, then (FP32 halo path) the per-tile flags behind them
+    cudaMemsetAsync(w.own_count, 0, sizeof(int) * (no + 1 + (with_cand ? 0 : nt)), s);
+    cudaMemsetAsync(w.counters, 0, sizeof(int) * kCounters, s);
     IFEM_LAUNCH_CHECK();
     if (b.n_inst == 0 || b.N == 0)
         return cudaSuccess;
@@ -79,17 +81,24 @@ cudaError_t bin_impl(const TransferArgs &a, int det_sort, int with_cand)
     bin_kernel<real, false><<<gn, 256, 0, s>>>(b, a.g, w, (const real *)a.x, with_cand);
     IFEM_LAUNCH_CHECK();
     int nb = (int)((no + kScanBlock - 1) / kScanBlock);
-    scan_local_kernel<<<nb, kScanThreads, 0, s>>>(nt, no, w.cand_count, w.own_count, w.cand_off, w.own_off,
-                                                  w.scan_blocks);
+    // without candidate lists the local own offsets go to the cursors, and
+    // own_scatter_kernel writes the final offsets beside them
+    scan_local_kernel<<<nb, kScanThreads, 0, s>>>(with_cand ? nt : 0, no, w.cand_count, w.own_count, w.cand_off,
+                                                  with_cand ? w.own_off : w.own_cursor, w.scan_blocks,
+                                                  w.counters + 8, w.counters + 4);
     IFEM_LAUNCH_CHECK();
-    scan_blocks_kernel<<<1, 1024, 0, s>>>(nb, w.scan_blocks, w.counters + 4);
-    IFEM_LAUNCH_CHECK();
-    scan_finish_kernel<<<(unsigned)((no + 1 + 255) / 256), 256, 0, s>>>(nt, no, w);
-    IFEM_LAUNCH_CHECK();
-    bin_kernel<real, true><<<gn, 256, 0, s>>>(b, a.g, w, (const real *)a.x, with_cand);
-    IFEM_LAUNCH_CHECK();
-    if (!with_cand) {
-        own_tiles_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(nt, w);
+    if (with_cand) {
+        scan_finish_kernel<<<(unsigned)((no + 1 + 255) / 256), 256, 0, s>>>(nt, no, w);
+        IFEM_LAUNCH_CHECK();
+        bin_kernel<real, true><<<gn, 256, 0, s>>>(b, a.g, w, (const real *)a.x, with_cand);
+        IFEM_LAUNCH_CHECK();
+    } else {
+        if constexpr (!std::is_same<real, float>::value)
+            return cudaErrorInvalidValue;   // the one-pass own lists are FP32 only
+        // enough threads for every own-list offset as well as every node
+        const long long per_inst = ((no + 1 + 255) / 256 + b.n_inst - 1) / b.n_inst;
+        dim3 gs((unsigned)std::max<long long>(gn.x, per_inst), b.n_inst);
+        own_scatter_kernel<<<gs, 256, 0, s>>>(b, w, nt, no);
         IFEM_LAUNCH_CHECK();
     }
     if (det_sort) {
@@ -110,8 +119,8 @@ cudaError_t spread_impl(const TransferArgs &a)
 {
     const DevBatch &b = a.b;
     cudaStream_t s = a.stream;
-    // the fused halo transfer right after its binning: own_tiles_kernel cleared
-    // the per-tile sums and the binning the work counter
+    // the fused halo transfer right after its binning: own_scatter_kernel
+    // cleared the per-tile sums and the binning the work counter
     const bool cleared = a.binned && a.halo && a.u != nullptr && a.v != nullptr;
     if (!cleared)
         cudaMemsetAsync(a.w.red_tile, 0, sizeof(double) * 3 * a.g.n_tiles, s);

@@ -105,7 +105,31 @@ __device__ __forceinline__ int agg_append(int *count, int *cursor, int *list, lo
     return slot;
 }
 
+// One-pass own-list binning (FP32 halo path): lanes with the same key share
+// one atomic on its count, whose old value gives each lane its rank among
+// the key's nodes; the leader also marks the key's tile as owning nodes.
+// Every lane of the warp must call this. Returns -1 for invalid lanes.
+__device__ __forceinline__ int agg_rank(int *count, int *tile_flag, long long key, bool valid)
+{
+    const unsigned k = valid ? (unsigned)key : 0xffffffffu;
+    const unsigned grp = __match_any_sync(0xffffffffu, k);
+    if (!valid)
+        return -1;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (lane == leader) {
+        base = atomicAdd(&count[key], __popc(grp));
+        tile_flag[key / kOwnSub3] = 1;
+    }
+    base = __shfl_sync(grp, base, leader);
+    return base + __popc(grp & ((1u << lane) - 1u));
+}
+
 // FILL = false: count candidate / own pairs per tile; FILL = true: write them.
+// Without candidate lists (FP32 halo path) only the count pass runs: it also
+// ranks each node within its own-list key and keeps the node's record by
+// node, and own_scatter_kernel places both after the scan.
 // Block size must be a multiple of 32 (every lane reaches the warp votes).
 template <typename real, bool FILL>
 __global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restrict__ x, int with_cand)
@@ -140,13 +164,15 @@ __global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restr
               sbz = (c[2] - tile_start(oz, B.t)) >> 2;
     const long long own = (B.tile_base + ((long long)oz * B.T + oy) * B.T + ox) * kOwnSub3
                           + (sbz * kOwnSub + sby) * kOwnSub + sbx;
-    const int slot = agg_append<FILL>(w.own_count, w.own_cursor, w.own_nodes, own, ok, node);
     if (!with_cand) {
-        // halo-scatter spread: the node's fractional cell coordinates and its
-        // cell within the tile, beside its own-list entry (same arithmetic as
-        // node_cell, so the cell matches the tile it was binned into)
-        if constexpr (FILL && std::is_same<real, float>::value) {
-            if (slot >= 0) {
+        // the node's fractional cell coordinates and its cell within the tile
+        // (same arithmetic as node_cell, so the cell matches the tile it was
+        // binned into)
+        if constexpr (!FILL && std::is_same<real, float>::value) {
+            const int rank = agg_rank(w.own_count, w.own_flag, own, ok);
+            if (in)
+                w.node_key[node] = make_int2(ok ? (int)own : -1, rank);
+            if (ok) {
                 float fr[3];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
@@ -157,11 +183,12 @@ __global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restr
                 const unsigned pk = (unsigned)(c[0] - tile_start(ox, B.t)) |
                                     ((unsigned)(c[1] - tile_start(oy, B.t)) << 8) |
                                     ((unsigned)(c[2] - tile_start(oz, B.t)) << 16);
-                w.own_rec[slot] = make_float4(fr[0], fr[1], fr[2], __uint_as_float(pk));
+                w.node_rec[node] = make_float4(fr[0], fr[1], fr[2], __uint_as_float(pk));
             }
         }
         return;
     }
+    agg_append<FILL>(w.own_count, w.own_cursor, w.own_nodes, own, ok, node);
 #pragma unroll
     for (int slot = 0; slot < 8; ++slot) {
         const int ix = slot & 1, iy = (slot >> 1) & 1, iz = slot >> 2;
@@ -173,8 +200,10 @@ __global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restr
     }
 }
 
-// Exclusive scan of the per-tile counts (two lists at once), 3 passes:
-// block-local scan -> scan of block sums -> add + cursors + active lists.
+// Exclusive scan of the per-tile counts (two lists at once): block-local
+// scan, whose last block to finish scans the block sums -> add + cursors +
+// active lists (scan_finish_kernel; in the FP32 halo path
+// own_scatter_kernel adds the block offsets itself).
 
 __device__ inline int block_exclusive_scan(int v, int *sh, int &total)
 {
@@ -212,9 +241,10 @@ __device__ inline int block_exclusive_scan(int v, int *sh, int &total)
 
 static __global__ void scan_local_kernel(long long n1, long long n2, const int *__restrict__ c1,
                                          const int *__restrict__ c2, int *__restrict__ o1, int *__restrict__ o2,
-                                         int *__restrict__ bsum)
+                                         int *__restrict__ bsum, int *__restrict__ ticket, int *__restrict__ totals)
 {
     __shared__ int sh[33];
+    __shared__ int last;
     long long base = (long long)blockIdx.x * kScanBlock + (long long)threadIdx.x * kScanPer;
     int v1[kScanPer], v2[kScanPer], s1 = 0, s2 = 0;
 #pragma unroll
@@ -238,28 +268,32 @@ static __global__ void scan_local_kernel(long long n1, long long n2, const int *
         e1 += v1[q];
         e2 += v2[q];
     }
+    // block sums out, then a ticket: the block that takes the last one sees
+    // every block's sum (fence before the ticket, L2 loads after it)
     if (threadIdx.x == 0) {
         bsum[2 * blockIdx.x] = t1;
         bsum[2 * blockIdx.x + 1] = t2;
+        __threadfence();
+        last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
     }
-}
-
-static __global__ void scan_blocks_kernel(int nb, int *__restrict__ bsum, int *__restrict__ totals)
-{
-    __shared__ int sh[33];
+    __syncthreads();
+    if (!last)
+        return;
+    __threadfence();
+    const int nb = (int)gridDim.x;
     int run1 = 0, run2 = 0;
-    for (int base = 0; base < nb; base += blockDim.x) {
-        int i = base + threadIdx.x;
-        int v1 = i < nb ? bsum[2 * i] : 0, v2 = i < nb ? bsum[2 * i + 1] : 0;
-        int t1, t2;
-        int e1 = block_exclusive_scan(v1, sh, t1);
-        int e2 = block_exclusive_scan(v2, sh, t2);
+    for (int b0 = 0; b0 < nb; b0 += blockDim.x) {
+        const int i = b0 + threadIdx.x;
+        const int u1 = i < nb ? __ldcg(&bsum[2 * i]) : 0, u2 = i < nb ? __ldcg(&bsum[2 * i + 1]) : 0;
+        int w1, w2;
+        const int x1 = block_exclusive_scan(u1, sh, w1);
+        const int x2 = block_exclusive_scan(u2, sh, w2);
         if (i < nb) {
-            bsum[2 * i] = e1 + run1;
-            bsum[2 * i + 1] = e2 + run2;
+            bsum[2 * i] = x1 + run1;
+            bsum[2 * i + 1] = x2 + run2;
         }
-        run1 += t1;
-        run2 += t2;
+        run1 += w1;
+        run2 += w2;
     }
     if (threadIdx.x == 0) {
         totals[0] = run1;
@@ -787,6 +821,12 @@ __global__ void __launch_bounds__(256) spread_fast_kernel(DevBatch b, DevGrid g,
 // value to the grid with L2 reductions, where neighbouring tiles' halos
 // combine atomically (summation order of a value across tiles is not fixed).
 // ST_TOUCHED counts the non-zero sums inside the tile itself.
+// INTERP = true fuses the interpolation S of the same step: each (node,
+// lattice) unit also gathers u at the 64 stencil points with the unscaled
+// weights it has just computed, v_d = sum phi u_d (Algorithm step 4).
+// AB2 = true (with INTERP) also takes the position update of Eq.
+// Bashforth_eqn from the velocity it has just gathered, out of place:
+// xn_d = x_d + dt (3/2 v_d - 1/2 vp_d), rounded as in ab2_kernel.
 constexpr int kHaloX = 4, kHaloYZ = 2;
 
 // Buffer pitches: the row pitch is 8 mod 16 and the plane pitch 4 mod 8, so
@@ -800,39 +840,53 @@ __host__ __device__ inline int halo_ints(int E)
     return halo_pp(E + 2 * kHaloYZ, px) * (E + 2 * kHaloYZ);
 }
 
-//
-// INTERP = true fuses the interpolation S of the same step: each (node,
-// lattice) unit also gathers u at the 64 stencil points with the unscaled
-// weights it has just computed, v_d = sum phi u_d (Algorithm step 4).
-// AB2 = true (with INTERP) also takes the position update of Eq.
-// Bashforth_eqn from the velocity it has just gathered, out of place:
-// xn_d = x_d + dt (3/2 v_d - 1/2 vp_d), rounded as in ab2_kernel.
-// Tiles with own nodes, compacted (FP32 halo path): the fused transfer
-// kernel takes its (tile, lattice) items from this list, so no CTA walks
-// empty tiles; counters[3] receives the number of listed tiles. The list
-// keeps roughly the tile order, so items running at the same time are
-// spatial neighbours whose velocity rows and grid lines share L2 (listing
-// the largest tiles first measured slower). The per-tile FP64 sums of the
-// spread are cleared here for every tile (the transfer writes them for the
-// listed tiles only).
-static __global__ void own_tiles_kernel(long long n_tiles, DevWork w)
+// FP32 halo path, after the scan: every binned node goes to its slot (the
+// scanned offset of its key plus its rank from the count pass) with its
+// record; the own-list offsets are finalised (local offset + block offset,
+// the total at the end); the per-tile FP64 sums of the spread are cleared
+// for every tile (the transfer writes them for the listed tiles only) and
+// the tiles that own nodes are listed, counters[3] of them. The fused
+// transfer kernels take their (tile, lattice) items from that list, so no
+// CTA walks empty tiles; it keeps roughly the tile order (in order within
+// each warp's append), so items running at the same time are spatial
+// neighbours whose velocity rows and grid lines share L2 (listing the
+// largest tiles first measured slower). Grid: the nodes of instance
+// blockIdx.y along x, at least n_own + 1 threads in all.
+static __global__ void own_scatter_kernel(DevBatch b, DevWork w, long long n_tiles, long long n_own)
 {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    bool has = false;
-    if (t < n_tiles) {
-        has = w.own_off[(t + 1) * kOwnSub3] > w.own_off[t * kOwnSub3];
-        w.red_tile[3 * t] = 0.0;
-        w.red_tile[3 * t + 1] = 0.0;
-        w.red_tile[3 * t + 2] = 0.0;
+    const InstDev I = b.inst[blockIdx.y];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < I.n_nodes) {
+        const int node = I.node_off + k;
+        const int2 kr = w.node_key[node];
+        if (kr.x >= 0) {
+            const int slot = w.own_cursor[kr.x] + w.scan_blocks[2 * (kr.x / kScanBlock) + 1] + kr.y;
+            w.own_nodes[slot] = node;
+            w.own_rec[slot] = w.node_rec[node];
+        }
     }
-    const unsigned m = __ballot_sync(0xffffffffu, has);
+    const long long nthr = (long long)gridDim.x * gridDim.y * blockDim.x;
+    const long long tid = ((long long)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
+    for (long long i = tid; i <= n_own; i += nthr)
+        w.own_off[i] = i < n_own ? w.own_cursor[i] + w.scan_blocks[2 * (i / kScanBlock) + 1] : w.counters[5];
     const int lane = threadIdx.x & 31;
-    int base = 0;
-    if (lane == 0 && m)
-        base = atomicAdd(&w.counters[3], __popc(m));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (has)
-        w.own_tiles[base + __popc(m & ((1u << lane) - 1u))] = (int)t;
+    for (long long t0 = tid - lane; t0 < n_tiles; t0 += nthr) {   // warp-uniform bounds
+        const long long t = t0 + lane;
+        bool has = false;
+        if (t < n_tiles) {
+            has = w.own_flag[t] != 0;
+            w.red_tile[3 * t] = 0.0;
+            w.red_tile[3 * t + 1] = 0.0;
+            w.red_tile[3 * t + 2] = 0.0;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, has);
+        int base = 0;
+        if (lane == 0 && m)
+            base = atomicAdd(&w.counters[3], __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (has)
+            w.own_tiles[base + __popc(m & ((1u << lane) - 1u))] = (int)t;
+    }
 }
 
 // red.shared.add without a compiler memory clobber: for accumulators that
@@ -1327,7 +1381,7 @@ __global__ void __launch_bounds__(256, 5) spread_halo_kernel(DevBatch b, DevGrid
 // IFEM_SCATTER_ATOMIC, Peskin kernel, with the interpolation of the same
 // step fused (Algorithm steps 2 and 4 use the same stencil weights of the
 // same positions). Work item = (tile, lattice) over the tiles with own
-// nodes (own_tiles_kernel), taken from a global counter; thread 0 fetches
+// nodes (own_scatter_kernel), taken from a global counter; thread 0 fetches
 // the next item during the node loop. Two shared buffers per CTA: U, the
 // velocity values the item's stencils read (2 cells around the tile), and A,
 // the spread accumulator over the tile plus the halo of spread_halo_kernel
