@@ -660,7 +660,7 @@ def main():
         cpu = cpu_baseline_parallel(wl)
         cpu["single_thread"] = cpu_baseline_sample(wl)
     # bin (halo path: count + rank, scan, placement + list of tiles with own nodes; candidate path:
-    # count, 2 scan, fill), forces, spread, interp (or one fused launch), 2 reductions
+    # count, 2 scans, fill), forces, spread and interp (one fused launch on the halo path), 2 reductions
     launches_per_step = (3 if fused else 4) + 1 + (1 if fused else 2) + 2
     if scatter == I.IFEM_SCATTER_DET:
         launches_per_step += 3

@@ -56,18 +56,18 @@ __device__ inline TileInfo decode_tile(const DevGrid &g, long long tile)
 __device__ __forceinline__ float mac_off(int d, int a) { return a == d ? 0.f : 0.5f; }
 
 // ---------------------------------------------------------------- binning
+// Cell of a node from its coordinates xa (all finite: true, else the cell is
+// zero from the first non-finite axis on); s receives the lattice coordinates.
 template <typename real>
-__device__ inline bool node_cell(const InstDev &I, const BoxDev &B, const real *x, long long N, int node,
-                                 int c[3])
+__device__ inline bool node_cell_xyz(const InstDev &I, const BoxDev &B, const real xa[3], int c[3], real s[3])
 {
     bool ok = true;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        real xa = x[a * N + node];
-        ok = ok && isfinite(xa);
+        ok = ok && isfinite(xa[a]);
         int I0;
-        real s = LatCoord<real>::get(I, B, a, xa, real(0), I0);
-        long long ci = (long long)I0 + (long long)floor(s);
+        s[a] = LatCoord<real>::get(I, B, a, xa[a], real(0), I0);
+        long long ci = (long long)I0 + (long long)floor(s[a]);
         int cw;
         if (ci >= 0 && ci < 2LL * B.n)
             cw = ci >= B.n ? (int)ci - B.n : (int)ci;
@@ -76,6 +76,26 @@ __device__ inline bool node_cell(const InstDev &I, const BoxDev &B, const real *
         c[a] = ok ? cw : 0;
     }
     return ok;
+}
+
+template <typename real>
+__device__ inline bool node_cell(const InstDev &I, const BoxDev &B, const real *x, long long N, int node,
+                                 int c[3])
+{
+    const real xa[3] = {x[node], x[N + node], x[2 * N + node]};
+    real s[3];
+    return node_cell_xyz<real>(I, B, xa, c, s);
+}
+
+// Own-list key of a cell: (tile, 4^3 sub-block of the tile). Nodes come out
+// of the binning grouped by position, which keeps the gathers of
+// neighbouring lanes on shared cache lines.
+__device__ __forceinline__ long long own_key(const BoxDev &B, const int c[3])
+{
+    const int ox = tile_of(c[0], B.t, B.T), oy = tile_of(c[1], B.t, B.T), oz = tile_of(c[2], B.t, B.T);
+    const int sbx = (c[0] - tile_start(ox, B.t)) >> 2, sby = (c[1] - tile_start(oy, B.t)) >> 2,
+              sbz = (c[2] - tile_start(oz, B.t)) >> 2;
+    return (B.tile_base + ((long long)oz * B.T + oy) * B.T + ox) * kOwnSub3 + (sbz * kOwnSub + sby) * kOwnSub + sbx;
 }
 
 // Warp-aggregated list append: lanes with the same tile share one global
@@ -126,6 +146,36 @@ __device__ __forceinline__ int agg_rank(int *count, int *tile_flag, long long ke
     return base + __popc(grp & ((1u << lane) - 1u));
 }
 
+// One-pass own-list binning of one node from its coordinates xa (FP32 halo
+// path; warp-collective, lanes with in = false take part): the node's rank
+// within its own-list key and its record -- fractional lattice coordinates
+// and cell within the tile, 8-bit x | y << 8 | z << 16 -- kept by node for
+// own_scatter_kernel. Nodes that are not finite or not in the box get the key
+// -1 and are counted in ST_DOMAIN.
+__device__ __forceinline__ void own_rank_node(const InstDev &I, const BoxDev &B, const DevWork &w, const float xa[3],
+                                              int node, bool in)
+{
+    int c[3] = {0, 0, 0};
+    float sl[3] = {0.f, 0.f, 0.f};
+    bool ok = false;
+    if (in) {
+        ok = node_cell_xyz<float>(I, B, xa, c, sl);
+        if (!ok)
+            status_add(w.status, ST_DOMAIN, 1);
+    }
+    const long long own = own_key(B, c);
+    const int rank = agg_rank(w.own_count, w.own_flag, own, ok);
+    if (in)
+        w.node_key[node] = make_int2(ok ? (int)own : -1, rank);
+    if (ok) {
+        const int ox = tile_of(c[0], B.t, B.T), oy = tile_of(c[1], B.t, B.T), oz = tile_of(c[2], B.t, B.T);
+        const unsigned pk = (unsigned)(c[0] - tile_start(ox, B.t)) | ((unsigned)(c[1] - tile_start(oy, B.t)) << 8) |
+                            ((unsigned)(c[2] - tile_start(oz, B.t)) << 16);
+        w.node_rec[node] = make_float4(sl[0] - floorf(sl[0]), sl[1] - floorf(sl[1]), sl[2] - floorf(sl[2]),
+                                       __uint_as_float(pk));
+    }
+}
+
 // FILL = false: count candidate / own pairs per tile; FILL = true: write them.
 // Without candidate lists (FP32 halo path) only the count pass runs: it also
 // ranks each node within its own-list key and keeps the node's record by
@@ -139,6 +189,18 @@ __global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restr
     const bool in = k < I.n_nodes;
     const BoxDev B = g.boxes[I.box];
     const int node = I.node_off + (in ? k : 0);
+    if (!with_cand) {
+        if constexpr (!FILL && std::is_same<real, float>::value) {
+            float xa[3] = {0.f, 0.f, 0.f};
+            if (in) {
+                xa[0] = x[node];
+                xa[1] = x[b.N + node];
+                xa[2] = x[2 * b.N + node];
+            }
+            own_rank_node(I, B, w, xa, node, in);
+        }
+        return;
+    }
     int c[3] = {0, 0, 0};
     bool ok = false;
     if (in) {
@@ -156,39 +218,7 @@ __global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restr
         tl[a][1] = tile_of(hi, B.t, B.T);
         nt[a] = tl[a][0] == tl[a][1] ? 1 : 2;
     }
-    // own lists are keyed by (tile, 4^3 sub-block of the tile): nodes then come
-    // out of the fill grouped by position, which keeps the interpolation's
-    // gathers of neighbouring lanes on shared cache lines
-    const int ox = tile_of(c[0], B.t, B.T), oy = tile_of(c[1], B.t, B.T), oz = tile_of(c[2], B.t, B.T);
-    const int sbx = (c[0] - tile_start(ox, B.t)) >> 2, sby = (c[1] - tile_start(oy, B.t)) >> 2,
-              sbz = (c[2] - tile_start(oz, B.t)) >> 2;
-    const long long own = (B.tile_base + ((long long)oz * B.T + oy) * B.T + ox) * kOwnSub3
-                          + (sbz * kOwnSub + sby) * kOwnSub + sbx;
-    if (!with_cand) {
-        // the node's fractional cell coordinates and its cell within the tile
-        // (same arithmetic as node_cell, so the cell matches the tile it was
-        // binned into)
-        if constexpr (!FILL && std::is_same<real, float>::value) {
-            const int rank = agg_rank(w.own_count, w.own_flag, own, ok);
-            if (in)
-                w.node_key[node] = make_int2(ok ? (int)own : -1, rank);
-            if (ok) {
-                float fr[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    int I0;
-                    const float t = LatCoord<float>::get(I, B, a, x[a * b.N + node], 0.f, I0);
-                    fr[a] = t - floorf(t);
-                }
-                const unsigned pk = (unsigned)(c[0] - tile_start(ox, B.t)) |
-                                    ((unsigned)(c[1] - tile_start(oy, B.t)) << 8) |
-                                    ((unsigned)(c[2] - tile_start(oz, B.t)) << 16);
-                w.node_rec[node] = make_float4(fr[0], fr[1], fr[2], __uint_as_float(pk));
-            }
-        }
-        return;
-    }
-    agg_append<FILL>(w.own_count, w.own_cursor, w.own_nodes, own, ok, node);
+    agg_append<FILL>(w.own_count, w.own_cursor, w.own_nodes, own_key(B, c), ok, node);
 #pragma unroll
     for (int slot = 0; slot < 8; ++slot) {
         const int ix = slot & 1, iy = (slot >> 1) & 1, iz = slot >> 2;
@@ -2264,7 +2294,58 @@ __device__ inline double block_sum(double v, double *sh)
 // parts selects what one launch writes: 1 the x/F sums (centroid, sum F,
 // torque: entries 0..8), 2 sum v (entries 9..11) and the box blocks, 3 all;
 // the sums of one quantity do not depend on parts.
+
 constexpr int kReduceThreads = 256;
+
+// Float-pair partials of one node's x, F and x (x) F terms (the x/F sums).
+__device__ __forceinline__ void df_add_xF(DF q[9], const float xk[3], const float Fk[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        df_add(q[a], xk[a]);
+        df_add(q[3 + a], Fk[a]);
+    }
+    df_add_prod(q[6], xk[1], Fk[2]);
+    df_add_prod(q[6], -xk[2], Fk[1]);
+    df_add_prod(q[7], xk[2], Fk[0]);
+    df_add_prod(q[7], -xk[0], Fk[2]);
+    df_add_prod(q[8], xk[0], Fk[1]);
+    df_add_prod(q[8], -xk[1], Fk[0]);
+}
+
+// Fixed-order total of kReduceThreads float-pair partials (one warp: lane
+// sums over a stride of 32, then a shuffle tree); the value is in lane 0.
+__device__ __forceinline__ double df_row_total(const float2 *row, int lane)
+{
+    DF s{0.f, 0.f};
+    for (int k = lane; k < kReduceThreads; k += 32) {
+        const float2 e = row[k];
+        df_add_df(s, DF{e.x, e.y});
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const DF y{__shfl_down_sync(0xffffffffu, s.hi, o), __shfl_down_sync(0xffffffffu, s.lo, o)};
+        df_add_df(s, y);
+    }
+    return (double)s.hi + (double)s.lo;
+}
+
+// Entries 0..8 of a particle's sums from the totals of x, F and x (x) F:
+// centroid, sum F, torque about the centroid, sum (x - c) x F = sum x x F - c x sum F.
+__device__ __forceinline__ void write_xF_sums(double *o, const double *tot, int n_nodes)
+{
+    const double c[3] = {tot[0] / n_nodes, tot[1] / n_nodes, tot[2] / n_nodes};
+    const double *S = tot + 3;
+    o[0] = c[0];
+    o[1] = c[1];
+    o[2] = c[2];
+    o[3] = S[0];
+    o[4] = S[1];
+    o[5] = S[2];
+    o[6] = tot[6] - (c[1] * S[2] - c[2] * S[1]);
+    o[7] = tot[7] - (c[2] * S[0] - c[0] * S[2]);
+    o[8] = tot[8] - (c[0] * S[1] - c[1] * S[0]);
+}
 
 template <typename real>
 __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(DevBatch b, DevGrid g,
@@ -2309,15 +2390,8 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(DevBatch b, DevG
                 for (int a = 0; a < 3; ++a) {
                     xk[a] = x[a * N + node];
                     Fk[a] = F ? F[a * N + node] : 0.f;
-                    df_add(q[a], xk[a]);
-                    df_add(q[3 + a], Fk[a]);
                 }
-                df_add_prod(q[6], xk[1], Fk[2]);
-                df_add_prod(q[6], -xk[2], Fk[1]);
-                df_add_prod(q[7], xk[2], Fk[0]);
-                df_add_prod(q[7], -xk[0], Fk[2]);
-                df_add_prod(q[8], xk[0], Fk[1]);
-                df_add_prod(q[8], -xk[1], Fk[0]);
+                df_add_xF(q, xk, Fk);
             }
         }
         if ((parts & 2) && v) {
@@ -2337,18 +2411,9 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(DevBatch b, DevG
             const bool want = i < 9 ? (parts & 1) != 0 : (parts & 2) != 0;
             if (!want)
                 continue;
-            DF s{0.f, 0.f};
-            for (int k = lane; k < (int)blockDim.x; k += 32) {
-                const float2 e = part[i][k];
-                df_add_df(s, DF{e.x, e.y});
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const DF y{__shfl_down_sync(0xffffffffu, s.hi, o), __shfl_down_sync(0xffffffffu, s.lo, o)};
-                df_add_df(s, y);
-            }
+            const double t = df_row_total(part[i], lane);
             if (lane == 0)
-                tot[i] = (double)s.hi + (double)s.lo;
+                tot[i] = t;
         }
     } else {
         double p[12];
@@ -2396,19 +2461,8 @@ __global__ void __launch_bounds__(kReduceThreads) reduce_kernel(DevBatch b, DevG
     __syncthreads();
     if (threadIdx.x == 0) {
         double *o = red + 12LL * blockIdx.x;
-        if (parts & 1) {
-            const double c[3] = {tot[0] / I.n_nodes, tot[1] / I.n_nodes, tot[2] / I.n_nodes};
-            const double *S = tot + 3;
-            o[0] = c[0];
-            o[1] = c[1];
-            o[2] = c[2];
-            o[3] = S[0];
-            o[4] = S[1];
-            o[5] = S[2];
-            o[6] = tot[6] - (c[1] * S[2] - c[2] * S[1]);
-            o[7] = tot[7] - (c[2] * S[0] - c[0] * S[2]);
-            o[8] = tot[8] - (c[0] * S[1] - c[1] * S[0]);
-        }
+        if (parts & 1)
+            write_xF_sums(o, tot, I.n_nodes);
         if (parts & 2) {
             o[9] = tot[9];
             o[10] = tot[10];
