@@ -120,7 +120,8 @@ struct DevWork {
     long long cand_cap;
     int *own_count;     // per (tile, 4^3 sub-block): n_tiles * kOwnSub3 + 1, then own_flag
     int *own_flag;      // n_tiles (FP32 halo path): 1 where the tile owns a node
-    int *own_off;
+    int *own_off;       // n_tiles * kOwnSub3 + 1 offsets; the FP32 halo path finalises the tile
+                        // boundaries only (entries t * kOwnSub3)
     int *own_cursor;    // fill cursors; local (per scan block) offsets in the FP32 halo path
     int *own_nodes;     // N entries: nodes grouped by the tile (and sub-block) of their cell
     float4 *own_rec;    // beside own_nodes (FP32 halo path): fractional cell coordinates x, y, z of

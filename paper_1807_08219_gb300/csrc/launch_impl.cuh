@@ -78,7 +78,16 @@ cudaError_t bin_impl(const TransferArgs &a, int det_sort, int with_cand)
     if (b.n_inst == 0 || b.N == 0)
         return cudaSuccess;
     dim3 gn((b.max_nodes + 255) / 256, b.n_inst);
-    bin_kernel<real, false><<<gn, 256, 0, s>>>(b, a.g, w, (const real *)a.x, with_cand);
+    // one-pass binning of the FP32 halo path: kBinPer nodes per thread
+    dim3 g1((b.max_nodes + 256 * kBinPer - 1) / (256 * kBinPer), b.n_inst);
+    if (with_cand) {
+        bin_kernel<real, false><<<gn, 256, 0, s>>>(b, a.g, w, (const real *)a.x);
+    } else {
+        if constexpr (!std::is_same<real, float>::value)
+            return cudaErrorInvalidValue;   // the one-pass own lists are FP32 only
+        else
+            own_count_kernel<<<g1, 256, 0, s>>>(b, a.g, w, (const float *)a.x);
+    }
     IFEM_LAUNCH_CHECK();
     int nb = (int)((no + kScanBlock - 1) / kScanBlock);
     // without candidate lists the local own offsets go to the cursors, and
@@ -90,15 +99,13 @@ cudaError_t bin_impl(const TransferArgs &a, int det_sort, int with_cand)
     if (with_cand) {
         scan_finish_kernel<<<(unsigned)((no + 1 + 255) / 256), 256, 0, s>>>(nt, no, w);
         IFEM_LAUNCH_CHECK();
-        bin_kernel<real, true><<<gn, 256, 0, s>>>(b, a.g, w, (const real *)a.x, with_cand);
+        bin_kernel<real, true><<<gn, 256, 0, s>>>(b, a.g, w, (const real *)a.x);
         IFEM_LAUNCH_CHECK();
     } else {
-        if constexpr (!std::is_same<real, float>::value)
-            return cudaErrorInvalidValue;   // the one-pass own lists are FP32 only
-        // enough threads for every own-list offset as well as every node
-        const long long per_inst = ((no + 1 + 255) / 256 + b.n_inst - 1) / b.n_inst;
-        dim3 gs((unsigned)std::max<long long>(gn.x, per_inst), b.n_inst);
-        own_scatter_kernel<<<gs, 256, 0, s>>>(b, w, nt, no);
+        // enough threads for every tile boundary as well as every node
+        const long long per_inst = ((nt + 1 + 255) / 256 + b.n_inst - 1) / b.n_inst;
+        dim3 gs((unsigned)std::max<long long>(g1.x, per_inst), b.n_inst);
+        own_scatter_kernel<<<gs, 256, 0, s>>>(b, w, nt);
         IFEM_LAUNCH_CHECK();
     }
     if (det_sort) {

@@ -125,82 +125,91 @@ __device__ __forceinline__ int agg_append(int *count, int *cursor, int *list, lo
     return slot;
 }
 
-// One-pass own-list binning (FP32 halo path): lanes with the same key share
-// one atomic on its count, whose old value gives each lane its rank among
-// the key's nodes; the leader also marks the key's tile as owning nodes.
-// Every lane of the warp must call this. Returns -1 for invalid lanes.
-__device__ __forceinline__ int agg_rank(int *count, int *tile_flag, long long key, bool valid)
-{
-    const unsigned k = valid ? (unsigned)key : 0xffffffffu;
-    const unsigned grp = __match_any_sync(0xffffffffu, k);
-    if (!valid)
-        return -1;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(grp) - 1;
-    int base = 0;
-    if (lane == leader) {
-        base = atomicAdd(&count[key], __popc(grp));
-        tile_flag[key / kOwnSub3] = 1;
-    }
-    base = __shfl_sync(grp, base, leader);
-    return base + __popc(grp & ((1u << lane) - 1u));
-}
-
-// One-pass own-list binning of one node from its coordinates xa (FP32 halo
-// path; warp-collective, lanes with in = false take part): the node's rank
-// within its own-list key and its record -- fractional lattice coordinates
+// One-pass own-list binning (FP32 halo path): per node its rank within its
+// own-list key (the old value of the key's count, one atomic per group of
+// lanes with the same key) and its record -- fractional lattice coordinates
 // and cell within the tile, 8-bit x | y << 8 | z << 16 -- kept by node for
-// own_scatter_kernel. Nodes that are not finite or not in the box get the key
-// -1 and are counted in ST_DOMAIN.
-__device__ __forceinline__ void own_rank_node(const InstDev &I, const BoxDev &B, const DevWork &w, const float xa[3],
-                                              int node, bool in)
+// own_scatter_kernel; the leader of each group also marks the key's tile as
+// owning nodes. Nodes that are not finite or not in the box get the key -1
+// and are counted in ST_DOMAIN. kBinPer nodes per thread, node
+// (blockIdx.x * kBinPer + j) * blockDim.x + threadIdx.x of instance
+// blockIdx.y, each phase's loads, atomics and stores issued for all of them
+// before their results are used: with one node per thread the pass is a
+// chain of dependent latencies.
+constexpr int kBinPer = 4;
+static __global__ void __launch_bounds__(256) own_count_kernel(DevBatch b, DevGrid g, DevWork w, const float *__restrict__ x)
 {
-    int c[3] = {0, 0, 0};
-    float sl[3] = {0.f, 0.f, 0.f};
-    bool ok = false;
-    if (in) {
-        ok = node_cell_xyz<float>(I, B, xa, c, sl);
-        if (!ok)
-            status_add(w.status, ST_DOMAIN, 1);
+    const InstDev I = b.inst[blockIdx.y];
+    const BoxDev B = g.boxes[I.box];
+    const long long N = b.N;
+    const int lane = threadIdx.x & 31;
+    int node[kBinPer];
+    bool in[kBinPer];
+    float xa[kBinPer][3];
+#pragma unroll
+    for (int j = 0; j < kBinPer; ++j) {
+        const int k = (blockIdx.x * kBinPer + j) * blockDim.x + threadIdx.x;
+        in[j] = k < I.n_nodes;
+        node[j] = I.node_off + (in[j] ? k : 0);
+        xa[j][0] = xa[j][1] = xa[j][2] = 0.f;
+        if (in[j]) {
+            xa[j][0] = x[node[j]];
+            xa[j][1] = x[N + node[j]];
+            xa[j][2] = x[2 * N + node[j]];
+        }
     }
-    const long long own = own_key(B, c);
-    const int rank = agg_rank(w.own_count, w.own_flag, own, ok);
-    if (in)
-        w.node_key[node] = make_int2(ok ? (int)own : -1, rank);
-    if (ok) {
-        const int ox = tile_of(c[0], B.t, B.T), oy = tile_of(c[1], B.t, B.T), oz = tile_of(c[2], B.t, B.T);
-        const unsigned pk = (unsigned)(c[0] - tile_start(ox, B.t)) | ((unsigned)(c[1] - tile_start(oy, B.t)) << 8) |
-                            ((unsigned)(c[2] - tile_start(oz, B.t)) << 16);
-        w.node_rec[node] = make_float4(sl[0] - floorf(sl[0]), sl[1] - floorf(sl[1]), sl[2] - floorf(sl[2]),
-                                       __uint_as_float(pk));
+    bool ok[kBinPer];
+    long long key[kBinPer];
+#pragma unroll
+    for (int j = 0; j < kBinPer; ++j) {
+        int c[3] = {0, 0, 0};
+        float sl[3];
+        ok[j] = in[j] && node_cell_xyz<float>(I, B, xa[j], c, sl);
+        if (in[j] && !ok[j])
+            status_add(w.status, ST_DOMAIN, 1);
+        key[j] = own_key(B, c);
+        if (ok[j]) {
+            const int ox = tile_of(c[0], B.t, B.T), oy = tile_of(c[1], B.t, B.T), oz = tile_of(c[2], B.t, B.T);
+            const unsigned pk = (unsigned)(c[0] - tile_start(ox, B.t)) |
+                                ((unsigned)(c[1] - tile_start(oy, B.t)) << 8) |
+                                ((unsigned)(c[2] - tile_start(oz, B.t)) << 16);
+            w.node_rec[node[j]] = make_float4(sl[0] - floorf(sl[0]), sl[1] - floorf(sl[1]), sl[2] - floorf(sl[2]),
+                                              __uint_as_float(pk));
+        }
+    }
+    // every lane takes part in the votes and shuffles (invalid lanes form
+    // their own group under the key 0xffffffff, which no valid key reaches)
+    unsigned grp[kBinPer];
+    int base[kBinPer];
+#pragma unroll
+    for (int j = 0; j < kBinPer; ++j) {
+        grp[j] = __match_any_sync(0xffffffffu, ok[j] ? (unsigned)key[j] : 0xffffffffu);
+        base[j] = 0;
+        if (ok[j] && lane == __ffs(grp[j]) - 1) {
+            base[j] = atomicAdd(&w.own_count[key[j]], __popc(grp[j]));
+            w.own_flag[key[j] / kOwnSub3] = 1;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kBinPer; ++j) {
+        const int rank = __shfl_sync(0xffffffffu, base[j], __ffs(grp[j]) - 1) + __popc(grp[j] & ((1u << lane) - 1u));
+        if (in[j])
+            w.node_key[node[j]] = make_int2(ok[j] ? (int)key[j] : -1, rank);
     }
 }
 
-// FILL = false: count candidate / own pairs per tile; FILL = true: write them.
-// Without candidate lists (FP32 halo path) only the count pass runs: it also
-// ranks each node within its own-list key and keeps the node's record by
-// node, and own_scatter_kernel places both after the scan.
-// Block size must be a multiple of 32 (every lane reaches the warp votes).
+// FILL = false: count candidate / own pairs per tile; FILL = true: write them
+// (paths with candidate lists; the FP32 halo path bins with own_count_kernel
+// and own_scatter_kernel). Block size must be a multiple of 32 (every lane
+// reaches the warp votes).
 template <typename real, bool FILL>
-__global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restrict__ x, int with_cand)
+__global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restrict__ x)
 {
     const InstDev I = b.inst[blockIdx.y];
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const bool in = k < I.n_nodes;
     const BoxDev B = g.boxes[I.box];
     const int node = I.node_off + (in ? k : 0);
-    if (!with_cand) {
-        if constexpr (!FILL && std::is_same<real, float>::value) {
-            float xa[3] = {0.f, 0.f, 0.f};
-            if (in) {
-                xa[0] = x[node];
-                xa[1] = x[b.N + node];
-                xa[2] = x[2 * b.N + node];
-            }
-            own_rank_node(I, B, w, xa, node, in);
-        }
-        return;
-    }
     int c[3] = {0, 0, 0};
     bool ok = false;
     if (in) {
@@ -871,43 +880,62 @@ __host__ __device__ inline int halo_ints(int E)
 }
 
 // FP32 halo path, after the scan: every binned node goes to its slot (the
-// scanned offset of its key plus its rank from the count pass) with its
-// record; the own-list offsets are finalised (local offset + block offset,
-// the total at the end); the per-tile FP64 sums of the spread are cleared
-// for every tile (the transfer writes them for the listed tiles only) and
-// the tiles that own nodes are listed, counters[3] of them. The fused
-// transfer kernels take their (tile, lattice) items from that list, so no
-// CTA walks empty tiles; it keeps roughly the tile order (in order within
-// each warp's append), so items running at the same time are spatial
-// neighbours whose velocity rows and grid lines share L2 (listing the
-// largest tiles first measured slower). Grid: the nodes of instance
-// blockIdx.y along x, at least n_own + 1 threads in all.
-static __global__ void own_scatter_kernel(DevBatch b, DevWork w, long long n_tiles, long long n_own)
+// scanned offset of its key plus its rank from own_count_kernel) with its
+// record, kBinPer nodes per thread as in own_count_kernel (loads first, then
+// the offsets, then the stores); the tile boundaries of the own lists are
+// finalised (own_off[t * kOwnSub3] = local offset + block offset, the total
+// at t = n_tiles: the only entries the halo kernels read); the per-tile FP64
+// sums of the spread are cleared for every tile (the transfer writes them
+// for the listed tiles only) and the tiles that own nodes are listed,
+// counters[3] of them. The fused transfer kernels take their (tile,
+// lattice) items from that list, so no CTA walks empty tiles; it keeps
+// roughly the tile order (in order within each warp's append), so items
+// running at the same time are spatial neighbours whose velocity rows and
+// grid lines share L2 (listing the largest tiles first measured slower).
+// Grid: as own_count_kernel along x and y, at least n_tiles + 1 threads in all.
+static __global__ void __launch_bounds__(256) own_scatter_kernel(DevBatch b, DevWork w, long long n_tiles)
 {
     const InstDev I = b.inst[blockIdx.y];
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < I.n_nodes) {
-        const int node = I.node_off + k;
-        const int2 kr = w.node_key[node];
-        if (kr.x >= 0) {
-            const int slot = w.own_cursor[kr.x] + w.scan_blocks[2 * (kr.x / kScanBlock) + 1] + kr.y;
-            w.own_nodes[slot] = node;
-            w.own_rec[slot] = w.node_rec[node];
+    int node[kBinPer];
+    int2 kr[kBinPer];
+    float4 rec[kBinPer];
+#pragma unroll
+    for (int j = 0; j < kBinPer; ++j) {
+        const int k = (blockIdx.x * kBinPer + j) * blockDim.x + threadIdx.x;
+        node[j] = I.node_off + k;
+        kr[j] = make_int2(-1, 0);
+        if (k < I.n_nodes) {
+            kr[j] = w.node_key[node[j]];
+            rec[j] = w.node_rec[node[j]];
+        }
+    }
+    int off[kBinPer];
+#pragma unroll
+    for (int j = 0; j < kBinPer; ++j)
+        off[j] = kr[j].x >= 0 ? w.own_cursor[kr[j].x] + w.scan_blocks[2 * (kr[j].x / kScanBlock) + 1] : 0;
+#pragma unroll
+    for (int j = 0; j < kBinPer; ++j) {
+        if (kr[j].x >= 0) {
+            const int slot = off[j] + kr[j].y;
+            w.own_nodes[slot] = node[j];
+            w.own_rec[slot] = rec[j];
         }
     }
     const long long nthr = (long long)gridDim.x * gridDim.y * blockDim.x;
     const long long tid = ((long long)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
-    for (long long i = tid; i <= n_own; i += nthr)
-        w.own_off[i] = i < n_own ? w.own_cursor[i] + w.scan_blocks[2 * (i / kScanBlock) + 1] : w.counters[5];
     const int lane = threadIdx.x & 31;
-    for (long long t0 = tid - lane; t0 < n_tiles; t0 += nthr) {   // warp-uniform bounds
+    for (long long t0 = tid - lane; t0 <= n_tiles; t0 += nthr) {   // warp-uniform bounds
         const long long t = t0 + lane;
         bool has = false;
         if (t < n_tiles) {
+            const long long i = t * kOwnSub3;
+            w.own_off[i] = w.own_cursor[i] + w.scan_blocks[2 * (i / kScanBlock) + 1];
             has = w.own_flag[t] != 0;
             w.red_tile[3 * t] = 0.0;
             w.red_tile[3 * t + 1] = 0.0;
             w.red_tile[3 * t + 2] = 0.0;
+        } else if (t == n_tiles) {
+            w.own_off[t * kOwnSub3] = w.counters[5];
         }
         const unsigned m = __ballot_sync(0xffffffffu, has);
         int base = 0;
