@@ -67,6 +67,24 @@ __device__ inline bool node_cell_xyz(const InstDev &I, const BoxDev &B, const re
         ok = ok && isfinite(xa[a]);
         int I0;
         s[a] = LatCoord<real>::get(I, B, a, xa[a], real(0), I0);
+        if constexpr (std::is_same<real, float>::value) {
+            // 32-bit integer arithmetic while the cell is within 2^30 of the
+            // particle's origin cell (every node near its box): the 64-bit
+            // path below kept the FP64 pipe 40 % busy in the binning pass
+            const float fl = floorf(s[a]);
+            if (fabsf(fl) < 1073741824.f && I0 > -1073741824 && I0 < 1073741824) {
+                const int ci = I0 + (int)fl;
+                int cw;
+                if (ci >= 0 && ci < 2 * B.n) {
+                    cw = ci >= B.n ? ci - B.n : ci;
+                } else {
+                    cw = ci % B.n;
+                    cw += cw < 0 ? B.n : 0;
+                }
+                c[a] = ok ? cw : 0;
+                continue;
+            }
+        }
         long long ci = (long long)I0 + (long long)floor(s[a]);
         int cw;
         if (ci >= 0 && ci < 2LL * B.n)
@@ -90,12 +108,18 @@ __device__ inline bool node_cell(const InstDev &I, const BoxDev &B, const real *
 // Own-list key of a cell: (tile, 4^3 sub-block of the tile). Nodes come out
 // of the binning grouped by position, which keeps the gathers of
 // neighbouring lanes on shared cache lines.
-__device__ __forceinline__ long long own_key(const BoxDev &B, const int c[3])
+// 32-bit: the workspace holds fewer than 2^31 - 1 keys (n_tiles * kOwnSub3,
+// checked when it is set up). r receives the cell within its tile.
+__device__ __forceinline__ int own_key(const BoxDev &B, const int c[3], int r[3])
 {
-    const int ox = tile_of(c[0], B.t, B.T), oy = tile_of(c[1], B.t, B.T), oz = tile_of(c[2], B.t, B.T);
-    const int sbx = (c[0] - tile_start(ox, B.t)) >> 2, sby = (c[1] - tile_start(oy, B.t)) >> 2,
-              sbz = (c[2] - tile_start(oz, B.t)) >> 2;
-    return (B.tile_base + ((long long)oz * B.T + oy) * B.T + ox) * kOwnSub3 + (sbz * kOwnSub + sby) * kOwnSub + sbx;
+    int o[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        o[a] = tile_of(c[a], B.t, B.T);
+        r[a] = c[a] - tile_start(o[a], B.t);
+    }
+    return ((int)B.tile_base + (o[2] * B.T + o[1]) * B.T + o[0]) * kOwnSub3 +
+           ((r[2] >> 2) * kOwnSub + (r[1] >> 2)) * kOwnSub + (r[0] >> 2);
 }
 
 // Warp-aggregated list append: lanes with the same tile share one global
@@ -159,7 +183,7 @@ static __global__ void __launch_bounds__(256) own_count_kernel(DevBatch b, DevGr
         }
     }
     bool ok[kBinPer];
-    long long key[kBinPer];
+    int key[kBinPer];
 #pragma unroll
     for (int j = 0; j < kBinPer; ++j) {
         int c[3] = {0, 0, 0};
@@ -167,12 +191,10 @@ static __global__ void __launch_bounds__(256) own_count_kernel(DevBatch b, DevGr
         ok[j] = in[j] && node_cell_xyz<float>(I, B, xa[j], c, sl);
         if (in[j] && !ok[j])
             status_add(w.status, ST_DOMAIN, 1);
-        key[j] = own_key(B, c);
+        int r[3];
+        key[j] = own_key(B, c, r);
         if (ok[j]) {
-            const int ox = tile_of(c[0], B.t, B.T), oy = tile_of(c[1], B.t, B.T), oz = tile_of(c[2], B.t, B.T);
-            const unsigned pk = (unsigned)(c[0] - tile_start(ox, B.t)) |
-                                ((unsigned)(c[1] - tile_start(oy, B.t)) << 8) |
-                                ((unsigned)(c[2] - tile_start(oz, B.t)) << 16);
+            const unsigned pk = (unsigned)r[0] | ((unsigned)r[1] << 8) | ((unsigned)r[2] << 16);
             w.node_rec[node[j]] = make_float4(sl[0] - floorf(sl[0]), sl[1] - floorf(sl[1]), sl[2] - floorf(sl[2]),
                                               __uint_as_float(pk));
         }
@@ -194,7 +216,7 @@ static __global__ void __launch_bounds__(256) own_count_kernel(DevBatch b, DevGr
     for (int j = 0; j < kBinPer; ++j) {
         const int rank = __shfl_sync(0xffffffffu, base[j], __ffs(grp[j]) - 1) + __popc(grp[j] & ((1u << lane) - 1u));
         if (in[j])
-            w.node_key[node[j]] = make_int2(ok[j] ? (int)key[j] : -1, rank);
+            w.node_key[node[j]] = make_int2(ok[j] ? key[j] : -1, rank);
     }
 }
 
@@ -227,7 +249,8 @@ __global__ void bin_kernel(DevBatch b, DevGrid g, DevWork w, const real *__restr
         tl[a][1] = tile_of(hi, B.t, B.T);
         nt[a] = tl[a][0] == tl[a][1] ? 1 : 2;
     }
-    agg_append<FILL>(w.own_count, w.own_cursor, w.own_nodes, own_key(B, c), ok, node);
+    int r[3];
+    agg_append<FILL>(w.own_count, w.own_cursor, w.own_nodes, own_key(B, c, r), ok, node);
 #pragma unroll
     for (int slot = 0; slot < 8; ++slot) {
         const int ix = slot & 1, iy = (slot >> 1) & 1, iz = slot >> 2;
