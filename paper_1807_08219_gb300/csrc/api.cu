@@ -816,7 +816,7 @@ static int do_spread(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
 // velocities it gathers (xn = x + dt (3/2 v - 1/2 vp)).
 static int do_spread_interp(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *F, const void *u,
                             void *f, void *v, int flags, void *stream, const void *vp = nullptr,
-                            void *xn = nullptr, double dt = 0.0, int lattice = -1)
+                            void *xn = nullptr, double dt = 0.0, int lattice = -1, int pdl = 0)
 {
     if (flags & IFEM_SPREAD_OVERWRITE) {
         cudaError_t e = cudaMemsetAsync(f, 0, (size_t)g->total * real_size(ctx), (cudaStream_t)stream);
@@ -827,8 +827,9 @@ static int do_spread_interp(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void 
     a.vp = vp;
     a.xn = xn;
     a.dt = dt;
-    a.binned = 1;   // every caller bins on this stream just before
+    a.binned = 1;   // every caller bins just before, on this stream or one joined to it
     a.lattice = lattice;
+    a.pdl = pdl;
     return launch_rc(ctx, launch_spread_f32(a), "spread + interpolate");
 }
 
@@ -1243,12 +1244,15 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
         return launch_rc(ctx, e, "step_coupling join");
     // with host arrays and the staged transfer, one launch per lattice: row d
     // of v goes back to the host on aux1 as soon as lattice d's launch ends,
-    // beside the later lattices
+    // beside the later lattices. Lattices 1 and 2 are launched with
+    // programmatic serialization: their CTAs start on the SMs that the
+    // previous lattice's CTAs leave once its items run out (they read nothing
+    // it writes), so the three launches share one tail instead of one each
     const bool v_rows = fused && io && ctx->staged && node_bytes > 0 && !(flags & IFEM_SPREAD_OVERWRITE);
     if (v_rows) {
         const size_t row = node_bytes / 3;
         for (int d = 0; d < 3; ++d) {
-            if ((rc = do_spread_interp(ctx, b, g, x, F, u, f, v, flags, stream, vp, xn, dt, d)) != IFEM_OK)
+            if ((rc = do_spread_interp(ctx, b, g, x, F, u, f, v, flags, stream, vp, xn, dt, d, d > 0)) != IFEM_OK)
                 return rc;
             if ((e = cudaEventRecord(ctx->fork[d == 2 ? 7 : 2 + d], s)) == cudaSuccess &&
                 (e = cudaStreamWaitEvent(ctx->aux[1], ctx->fork[d == 2 ? 7 : 2 + d], 0)) == cudaSuccess)
@@ -1257,6 +1261,10 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
             if (e != cudaSuccess)
                 return launch_rc(ctx, e, "step_coupling_host: copy out");
         }
+        // what follows on s waits for every lattice, not only the last one
+        if ((e = cudaStreamWaitEvent(s, ctx->fork[2], 0)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s, ctx->fork[3], 0)) != cudaSuccess)
+            return launch_rc(ctx, e, "step_coupling join");
         if ((e = cudaEventRecord(ctx->fork[8], ctx->aux[1])) != cudaSuccess)
             return launch_rc(ctx, e, "step_coupling_host: copy out");
     } else if (fused) {

@@ -358,6 +358,7 @@ struct TransferArgs {
     int binned;       // the binning of this step ran just before on the same stream (own tiles
                       // listed, work counter and per-tile sums cleared)
     int lattice;      // staged fused transfer: -1 all three lattices, else that lattice only
+    int pdl;          // staged fused transfer: may start before the previous kernel in the stream ends
     int use_wtab;     // FP64 Peskin interpolation: read the stencils the binning of x tabulated
     const void *vp;   // fused position update (halo spread + interpolation only):
     void *xn;         //   xn = x + dt (3/2 v - 1/2 vp) when xn is not null

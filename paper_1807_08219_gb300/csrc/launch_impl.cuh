@@ -149,12 +149,30 @@ cudaError_t spread_impl(const TransferArgs &a)
                 int occ = 1;
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kp, kStagedThreads, sm);
                 occ = occ < 1 ? 1 : occ;
-                kp<<<a.n_sm * occ, kStagedThreads, sm, s>>>(b, a.g, a.w, (const float *)a.x, (const float *)a.F,
-                                                          (float *)a.f, a.density, (const float *)a.u, (float *)a.v,
-                                                          (const float *)a.vp, (float *)a.xn, (float)a.dt,
-                                                          a.lattice);
-                IFEM_LAUNCH_CHECK();
-                return cudaSuccess;
+                if (!a.pdl) {
+                    kp<<<a.n_sm * occ, kStagedThreads, sm, s>>>(b, a.g, a.w, (const float *)a.x,
+                                                              (const float *)a.F, (float *)a.f, a.density,
+                                                              (const float *)a.u, (float *)a.v, (const float *)a.vp,
+                                                              (float *)a.xn, (float)a.dt, a.lattice);
+                    IFEM_LAUNCH_CHECK();
+                    return cudaSuccess;
+                }
+                // programmatic dependent launch: the CTAs of this grid may start once
+                // every CTA of the previous kernel in the stream has signalled
+                // (griddepcontrol.launch_dependents); they read nothing it writes
+                cudaLaunchConfig_t cfg{};
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                attr[0].val.programmaticStreamSerializationAllowed = 1;
+                cfg.gridDim = dim3(a.n_sm * occ);
+                cfg.blockDim = dim3(kStagedThreads);
+                cfg.dynamicSmemBytes = sm;
+                cfg.stream = s;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                return cudaLaunchKernelEx(&cfg, kp, b, a.g, a.w, (const float *)a.x, (const float *)a.F,
+                                          (float *)a.f, a.density, (const float *)a.u, (float *)a.v,
+                                          (const float *)a.vp, (float *)a.xn, (float)a.dt, a.lattice);
             }
             auto kern = !fused ? spread_halo_kernel<false>
                                : (a.xn ? spread_halo_kernel<true, true> : spread_halo_kernel<true>);

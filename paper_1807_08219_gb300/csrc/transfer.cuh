@@ -1634,6 +1634,12 @@ __global__ void __launch_bounds__(kStagedThreads, 3) transfer_staged_kernel(DevB
 
         // 2. next item's velocities and scale bound; flush of A
         const int next = s_item[slot ^ 1];
+        if (next < 0) {
+            // this CTA's last item: a kernel launched after this one with
+            // programmatic serialization (the next lattice of the same step)
+            // may start on the SMs that finished CTAs leave
+            asm volatile("griddepcontrol.launch_dependents;");
+        }
         if (next >= 0) {
             const PairItem nxt = pair_item(next, s_ti[slot ^ 1], s_B[slot ^ 1], density);
             pair_stage(nxt, u, sU);
