@@ -1246,7 +1246,7 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
     // of v goes back to the host on aux1 as soon as lattice d's launch ends,
     // beside the later lattices. Lattices 1 and 2 are launched with
     // programmatic serialization: their CTAs start on the SMs that the
-    // previous lattice's CTAs leave once its items run out (they read nothing
+    // previous lattice's CTAs leave when its items run out (they read nothing
     // it writes), so the three launches share one tail instead of one each
     const bool v_rows = fused && io && ctx->staged && node_bytes > 0 && !(flags & IFEM_SPREAD_OVERWRITE);
     if (v_rows) {

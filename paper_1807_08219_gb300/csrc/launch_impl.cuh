@@ -159,7 +159,8 @@ cudaError_t spread_impl(const TransferArgs &a)
                 }
                 // programmatic dependent launch: the CTAs of this grid may start once
                 // every CTA of the previous kernel in the stream has signalled
-                // (griddepcontrol.launch_dependents); they read nothing it writes
+                // (griddepcontrol.launch_dependents, at its start); they read
+                // nothing it writes
                 cudaLaunchConfig_t cfg{};
                 cudaLaunchAttribute attr[1];
                 attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

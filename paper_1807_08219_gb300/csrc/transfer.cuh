@@ -1509,6 +1509,11 @@ __global__ void __launch_bounds__(kStagedThreads, 3) transfer_staged_kernel(DevB
     const unsigned sU = smem_u32(pair_smem) + 8u, sA = smem_u32(pair_smem) + (unsigned)ubytes;
     const long long N = b.N;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // a kernel launched after this one with programmatic serialization (the
+    // next lattice of the same step, which reads nothing this one writes) may
+    // start at once: the grid is sized to be resident, so its CTAs take the
+    // SMs that this grid's CTAs leave when the items run out
+    asm volatile("griddepcontrol.launch_dependents;");
     for (int i = threadIdx.x; i < buf / 16; i += blockDim.x)
         reinterpret_cast<int4 *>(A)[i] = make_int4(0, 0, 0, 0);
     if (threadIdx.x == 0)
@@ -1634,12 +1639,6 @@ __global__ void __launch_bounds__(kStagedThreads, 3) transfer_staged_kernel(DevB
 
         // 2. next item's velocities and scale bound; flush of A
         const int next = s_item[slot ^ 1];
-        if (next < 0) {
-            // this CTA's last item: a kernel launched after this one with
-            // programmatic serialization (the next lattice of the same step)
-            // may start on the SMs that finished CTAs leave
-            asm volatile("griddepcontrol.launch_dependents;");
-        }
         if (next >= 0) {
             const PairItem nxt = pair_item(next, s_ti[slot ^ 1], s_B[slot ^ 1], density);
             pair_stage(nxt, u, sU);
