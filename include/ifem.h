@@ -417,7 +417,10 @@ int ifem_step_coupling_ab2(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *
  * kernel the fused spreading and interpolation then run as one launch per
  * lattice, and row d of v goes back to the host as soon as lattice d is done
  * (rows 0 and 1 beside the later lattices, row 2 beside the sums of v and the
- * boxes). Results equal those of copying x in, calling
+ * boxes); lattices 1 and 2 are launched with programmatic serialization, so
+ * that their blocks start as the previous lattice's run out of work (within
+ * stream capture this becomes a programmatic edge of the graph). Results
+ * equal those of copying x in, calling
  * ifem_step_coupling and copying v and red out. Returns IFEM_ERR_ARG for null
  * host arrays (N > 0) or red_host without red. */
 int ifem_step_coupling_host(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x_host, void *x,
