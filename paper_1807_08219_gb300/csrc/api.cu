@@ -1168,8 +1168,8 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
     // the forces' last blocks they slowed the binning's scan, which the
     // transfer waits for, while the transfer's CTAs take their work from a
     // counter and absorb them
-    //   s:    bin ----------------------- wait(forces) spread  wait(interp) wait(sums) sums of v, boxes
-    //   aux0: forces --/ wait(bin) sums of x, F -----------------------------/
+    //   s:    bin ----------------------- wait(forces) spread  wait(interp) sums of v, boxes  wait(sums)
+    //   aux0: forces --/ wait(bin) sums of x, F ---------------------------------------------/
     //   aux1:       wait(bin) interp [ab2] -------/
     // (with the fused spread + interpolation [+ ab2] the aux1 branch is absent).
     // With host arrays the positions arrive on s in two halves (by particle)
@@ -1287,10 +1287,12 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
             return launch_rc(ctx, e, "step_coupling_host: copy out");
     }
     if (red) {
-        if ((e = cudaStreamWaitEvent(s, ctx->fork[4], 0)) != cudaSuccess)
-            return launch_rc(ctx, e, "step_coupling join");
+        // the sums of v and the boxes write other entries than the x/F sums,
+        // which may still be running in the transfer's tail: join them after
         if ((rc = do_reduce(ctx, b, x, F, v, red, stream, 2)) != IFEM_OK)
             return rc;
+        if ((e = cudaStreamWaitEvent(s, ctx->fork[4], 0)) != cudaSuccess)
+            return launch_rc(ctx, e, "step_coupling join");
     }
     if (io && io->red_host &&
         (e = cudaMemcpyAsync(io->red_host, red, io->red_n * sizeof(double), cudaMemcpyDeviceToHost, s)) !=
