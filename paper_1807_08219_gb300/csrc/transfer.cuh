@@ -69,8 +69,9 @@ __device__ inline bool node_cell_xyz(const InstDev &I, const BoxDev &B, const re
         s[a] = LatCoord<real>::get(I, B, a, xa[a], real(0), I0);
         if constexpr (std::is_same<real, float>::value) {
             // 32-bit integer arithmetic while the cell is within 2^30 of the
-            // particle's origin cell (every node near its box): the 64-bit
-            // path below kept the FP64 pipe 40 % busy in the binning pass
+            // particle's origin cell (every node near its box): with 64-bit
+            // arithmetic for the cell and the own-list key the FP64 pipe was
+            // 40 % busy in the binning pass
             const float fl = floorf(s[a]);
             if (fabsf(fl) < 1073741824.f && I0 > -1073741824 && I0 < 1073741824) {
                 const int ci = I0 + (int)fl;

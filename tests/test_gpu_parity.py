@@ -221,6 +221,22 @@ def test_fp32_atomic_small_boxes(n, tile):
     assert rel_l2(g["v"], o["v"]) < TOL_V
 
 
+@pytest.mark.parametrize("org", [[0.999, 0.0005, 0.5], [1.3, -0.2, 5.0]])
+def test_fp32_atomic_particle_across_boundary_and_outside_box(org):
+    """FP32 ATOMIC Peskin path (one-pass binning, fused staged transfer) with
+    the particle across the periodic faces and with its origin outside [0, L)
+    (cells below 0 and beyond 2n, wrapped in 32-bit arithmetic)."""
+    import dataclasses
+    w = wl("C1")
+    ww = rounded_workload(dataclasses.replace(w, instances=[dataclasses.replace(w.instances[0], origin=np.array(org))]),
+                          np.float32)
+    g = run_gpu_step(ww, FP32, scatter=1)
+    o = oracle_step(ww)
+    assert g["rc"] == 0, g["stats"]
+    eF, ev, ef = rel_l2(g["F"], o["F"]), rel_l2(g["v"], o["v"]), rel_l2(g["f"][0], o["f"][0])
+    assert eF < TOL_F and ev < TOL_V and ef < TOL_GRID, (eF, ev, ef)
+
+
 @pytest.mark.parametrize("case", ["C2", "C3", "small"])
 def test_fp32_fused_gather_kernel(case, monkeypatch):
     """The fused transfer that gathers velocities through L1
