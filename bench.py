@@ -44,7 +44,7 @@ REF_BUDGET_S = 150.0   # --impl reference: warm-up + timed oracle steps
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the current kernels on the C4 suspension (profiles/*_c4_fp32.md),
 # reported for that workload only; set an entry to None when its kernel changes.
-NCU_TRAFFIC = {"spread+interp": 572.7e6, "spread": None, "interp": None, "forces": None, "bin": None}
+NCU_TRAFFIC = {"spread+interp": 607.4e6, "spread": None, "interp": None, "forces": None, "bin": None}
 # The unit that bounds each kernel in that capture and its fraction of peak (context for the HBM
 # fraction: the fused transfer kernel is latency-bound at 12 warps per SM, with the L1 load/store
 # pipe the busiest unit; the forces kernel is bound by shared-memory wavefronts).
