@@ -165,9 +165,11 @@ extern "C" int ifem_stage_times(ifem_ctx ctx, double *ms)
     if (!ctx || !ms || !ctx->ev_ok || !ctx->ev_recorded)
         return fail(ctx, IFEM_ERR_ARG, "stage_times: profiling off or no step recorded");
     CK(cudaEventSynchronize(ctx->ev[5]));
+    // the step records ev1, forces, ev0, binning, ev2, spread, ev3, interp, ev4, sums, ev5
+    const int from[5] = {0, 1, 2, 3, 4}, to[5] = {2, 0, 3, 4, 5};
     for (int i = 0; i < 5; ++i) {
         float t = 0.f;
-        CK(cudaEventElapsedTime(&t, ctx->ev[i], ctx->ev[i + 1]));
+        CK(cudaEventElapsedTime(&t, ctx->ev[from[i]], ctx->ev[to[i]]));
         ms[i] = t;
     }
     if (ctx->ev_fused) {
@@ -674,8 +676,9 @@ static int ws_ensure(ifem_ctx ctx, ifem_batch b, ifem_grid g, int tile)
     CK(alloc((void **)&w.cand_off, sizeof(int) * (nt + 1)));
     CK(alloc((void **)&w.cand_cursor, sizeof(int) * (nt + 1)));
     CK(alloc((void **)&w.cand_nodes, sizeof(int) * (size_t)w.cand_cap));
-    CK(alloc((void **)&w.own_count, sizeof(int) * (no + 1 + nt)));
+    CK(alloc((void **)&w.own_count, sizeof(int) * (no + 1 + 4 * nt)));
     w.own_flag = w.own_count + no + 1;
+    w.tile_fsum = reinterpret_cast<float *>(w.own_flag + nt);
     CK(alloc((void **)&w.own_off, sizeof(int) * (no + 1)));
     CK(alloc((void **)&w.own_cursor, sizeof(int) * (no + 1)));
     CK(alloc((void **)&w.own_nodes, sizeof(int) * (size_t)std::max<long long>(N, 1)));
@@ -787,13 +790,18 @@ static int do_forces(ifem_ctx ctx, ifem_batch b, const void *x, void *F, const v
     return launch_rc(ctx, e, "forces");
 }
 
-static int do_bin(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, void *stream)
+// stages other than BIN_ALL: the FP32 halo path only. F (FP32 halo path):
+// the placement also sums |F| per tile, which the fused transfer requires
+// (every do_spread_interp follows a binning given the same forces).
+static int do_bin(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, void *stream, int stages = BIN_ALL,
+                  const void *F = nullptr)
 {
     int rc = ws_ensure(ctx, b, g, ctx->tile);
     if (rc != IFEM_OK)
         return rc;
-    TransferArgs a = transfer_args(ctx, b, x, nullptr, nullptr, nullptr, nullptr, 0, stream);
-    cudaError_t e = ctx->cfg.precision == IFEM_FP64 ? launch_bin_f64(a, 1, 1) : launch_bin_f32(a, 0, !use_halo(ctx));
+    TransferArgs a = transfer_args(ctx, b, x, F, nullptr, nullptr, nullptr, 0, stream);
+    cudaError_t e = ctx->cfg.precision == IFEM_FP64 ? launch_bin_f64(a, 1, 1, stages)
+                                                    : launch_bin_f32(a, 0, !use_halo(ctx), stages);
     return launch_rc(ctx, e, "binning");
 }
 
@@ -1126,11 +1134,13 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
         // interpolation; host copies lie outside the stages)
         if (io && (e = copy_nodes_in(ctx, b, io->x_host, const_cast<void *>(x), 0, b->N, s)) != cudaSuccess)
             return launch_rc(ctx, e, "step_coupling_host: copy in");
-        mark(ctx, 0, stream);
-        if ((rc = do_bin(ctx, b, g, x, stream)) != IFEM_OK)
-            return rc;
+        // forces (ev1 -> ev0), then the binning (ev0 -> ev2): the fused
+        // transfer's placement sums the forces per tile
         mark(ctx, 1, stream);
         if ((rc = do_forces(ctx, b, x, F, nullptr, 0, stream)) != IFEM_OK)
+            return rc;
+        mark(ctx, 0, stream);
+        if ((rc = do_bin(ctx, b, g, x, stream, BIN_ALL, F)) != IFEM_OK)
             return rc;
         mark(ctx, 2, stream);
         ctx->ev_fused = use_halo(ctx);
@@ -1171,13 +1181,17 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
     //   s:    bin ----------------------- wait(forces) spread  wait(interp) sums of v, boxes  wait(sums)
     //   aux0: forces --/ wait(bin) sums of x, F ---------------------------------------------/
     //   aux1:       wait(bin) interp [ab2] -------/
-    // (with the fused spread + interpolation [+ ab2] the aux1 branch is absent).
+    // With the fused spread + interpolation [+ ab2] the aux1 branch is absent,
+    // and the binning's placement, which sums |F| per tile for the transfer's
+    // fixed-point scales, waits for the forces:
+    //   s:    count, scan -- wait(forces) placement  spread+interp  sums of v, boxes  wait(sums)
+    //   aux0: forces ------/ wait(placement) sums of x, F ------------------------------/
     // With host arrays the positions arrive on s in two halves (by particle)
     // when the force kernel takes particle ranges, each half's forces starting
     // on aux0 once it has landed; v goes back to the host on aux1 beside the
     // sums of v and the boxes:
-    //   s:    copy x[0:h] copy x[h:N] bin ... spread+interp  sums of v, boxes  copy red  wait(copy v)
-    //   aux0:   wait(x[0:h]) forces[0:h] wait(x[h:N]) forces[h:N] wait(bin) sums of x, F
+    //   s:    copy x[0:h] copy x[h:N] count, scan, wait(forces) placement ... spread+interp  sums of v, boxes  copy red  wait(copy v)
+    //   aux0:   wait(x[0:h]) forces[0:h] wait(x[h:N]) forces[h:N] wait(placement) sums of x, F
     //   aux1:                                           wait(v) copy v ------------------/
     const bool fused = use_halo(ctx) != 0;
     if ((rc = ws_ensure(ctx, b, g, ctx->tile)) != IFEM_OK)
@@ -1216,8 +1230,16 @@ static int step_impl(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, con
     }
     if ((e = cudaEventRecord(ctx->fork[1], ctx->aux[0])) != cudaSuccess)
         return launch_rc(ctx, e, "step_coupling fork");
-    if ((rc = do_bin(ctx, b, g, x, stream)) != IFEM_OK)
+    // with the fused transfer the binning's count and scan run beside the
+    // forces and its placement (which sums the forces per tile) after them
+    if ((rc = do_bin(ctx, b, g, x, stream, fused ? BIN_COUNT : BIN_ALL)) != IFEM_OK)
         return rc;
+    if (fused) {
+        if ((e = cudaStreamWaitEvent(s, ctx->fork[1], 0)) != cudaSuccess)
+            return launch_rc(ctx, e, "step_coupling join");
+        if ((rc = do_bin(ctx, b, g, x, stream, BIN_PLACE, F)) != IFEM_OK)
+            return rc;
+    }
     // the x/F sums, after the forces and the binning, on aux0 beside the transfers
     if (red) {
         if ((e = cudaEventRecord(ctx->fork[9], s)) != cudaSuccess ||
@@ -1419,7 +1441,7 @@ static int autotune(ifem_ctx ctx, ifem_batch b, const void *x, void *stream)
         float tmin = 1e30f;
         for (int rep = 0; rep < 3 && rc == IFEM_OK; ++rep) {
             cudaEventRecord(e0, s);
-            if ((rc = do_bin(ctx, b, g, x, stream)) == IFEM_OK) {
+            if ((rc = do_bin(ctx, b, g, x, stream, BIN_ALL, F)) == IFEM_OK) {
                 // the transfer launches the step will use (fused where it fuses)
                 if (use_halo(ctx))
                     rc = do_spread_interp(ctx, b, g, x, F, u, f, v, 0, stream);

@@ -118,8 +118,10 @@ struct DevWork {
     int *cand_cursor;   // n_tiles
     int *cand_nodes;    // pair list: node id per (tile, node) candidate pair
     long long cand_cap;
-    int *own_count;     // per (tile, 4^3 sub-block): n_tiles * kOwnSub3 + 1, then own_flag
+    int *own_count;     // per (tile, 4^3 sub-block): n_tiles * kOwnSub3 + 1, then own_flag, tile_fsum
     int *own_flag;      // n_tiles (FP32 halo path): 1 where the tile owns a node
+    float *tile_fsum;   // 3 per tile (FP32 halo path): sum of |F_d| over the tile's own nodes, from the
+                        // placement when it is given the forces (the fused transfer's fixed-point scale)
     int *own_off;       // n_tiles * kOwnSub3 + 1 offsets; the FP32 halo path finalises the tile
                         // boundaries only (entries t * kOwnSub3)
     int *own_cursor;    // fill cursors; local (per scan block) offsets in the FP32 halo path
@@ -381,8 +383,12 @@ struct ReduceArgs {
 // Defined once per precision in kernels_f32.cu / kernels_f64.cu.
 cudaError_t launch_forces_f32(const ForcesArgs &a);
 cudaError_t launch_forces_f64(const ForcesArgs &a);
-cudaError_t launch_bin_f32(const TransferArgs &a, int det_sort, int with_cand);
-cudaError_t launch_bin_f64(const TransferArgs &a, int det_sort, int with_cand);
+// Binning in two parts: the clears, the count pass and the scan, then the
+// placement (which also sums |F| per tile when TransferArgs::F is given).
+// Only the FP32 halo path (with_cand = 0) takes them apart.
+enum BinStage { BIN_COUNT = 1, BIN_PLACE = 2, BIN_ALL = 3 };
+cudaError_t launch_bin_f32(const TransferArgs &a, int det_sort, int with_cand, int stages = BIN_ALL);
+cudaError_t launch_bin_f64(const TransferArgs &a, int det_sort, int with_cand, int stages = BIN_ALL);
 cudaError_t launch_spread_f32(const TransferArgs &a);
 cudaError_t launch_spread_f64(const TransferArgs &a);
 cudaError_t launch_interp_f32(const TransferArgs &a);

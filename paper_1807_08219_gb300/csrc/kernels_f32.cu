@@ -3,9 +3,9 @@
 
 namespace ifem {
 cudaError_t launch_forces_f32(const ForcesArgs &a) { return forces_impl<float>(a); }
-cudaError_t launch_bin_f32(const TransferArgs &a, int det_sort, int with_cand)
+cudaError_t launch_bin_f32(const TransferArgs &a, int det_sort, int with_cand, int stages)
 {
-    return bin_impl<float>(a, det_sort, with_cand);
+    return bin_impl<float>(a, det_sort, with_cand, stages);
 }
 cudaError_t launch_spread_f32(const TransferArgs &a) { return spread_impl<float>(a); }
 cudaError_t launch_interp_f32(const TransferArgs &a) { return interp_impl<float>(a); }

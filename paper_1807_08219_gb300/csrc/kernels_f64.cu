@@ -6,9 +6,9 @@
 
 namespace ifem {
 cudaError_t launch_forces_f64(const ForcesArgs &a) { return forces_impl<double>(a); }
-cudaError_t launch_bin_f64(const TransferArgs &a, int det_sort, int with_cand)
+cudaError_t launch_bin_f64(const TransferArgs &a, int det_sort, int with_cand, int stages)
 {
-    return bin_impl<double>(a, det_sort, with_cand);
+    return bin_impl<double>(a, det_sort, with_cand, stages);
 }
 cudaError_t launch_spread_f64(const TransferArgs &a) { return spread_impl<double>(a); }
 cudaError_t launch_interp_f64(const TransferArgs &a) { return interp_impl<double>(a); }

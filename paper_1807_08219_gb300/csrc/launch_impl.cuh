@@ -62,40 +62,47 @@ cudaError_t forces_impl(const ForcesArgs &a)
 }
 
 template <typename real>
-cudaError_t bin_impl(const TransferArgs &a, int det_sort, int with_cand)
+cudaError_t bin_impl(const TransferArgs &a, int det_sort, int with_cand, int stages)
 {
     const DevBatch &b = a.b;
     const DevWork &w = a.w;
     const long long nt = a.g.n_tiles;
     cudaStream_t s = a.stream;
     const long long no = nt * kOwnSub3;
-    if (with_cand)
-        cudaMemsetAsync(w.cand_count, 0, sizeof(int) * (nt + 1), s);
-    // own counts, then (FP32 halo path) the per-tile flags behind them
-    cudaMemsetAsync(w.own_count, 0, sizeof(int) * (no + 1 + (with_cand ? 0 : nt)), s);
-    cudaMemsetAsync(w.counters, 0, sizeof(int) * kCounters, s);
-    IFEM_LAUNCH_CHECK();
-    if (b.n_inst == 0 || b.N == 0)
-        return cudaSuccess;
+    if (with_cand && stages != BIN_ALL)
+        return cudaErrorInvalidValue;
+    const bool empty = b.n_inst == 0 || b.N == 0;
     dim3 gn((b.max_nodes + 255) / 256, b.n_inst);
     // one-pass binning of the FP32 halo path: kBinPer nodes per thread
     dim3 g1((b.max_nodes + 256 * kBinPer - 1) / (256 * kBinPer), b.n_inst);
-    if (with_cand) {
-        bin_kernel<real, false><<<gn, 256, 0, s>>>(b, a.g, w, (const real *)a.x);
-    } else {
-        if constexpr (!std::is_same<real, float>::value)
-            return cudaErrorInvalidValue;   // the one-pass own lists are FP32 only
-        else
-            own_count_kernel<<<g1, 256, 0, s>>>(b, a.g, w, (const float *)a.x);
+    if (stages & BIN_COUNT) {
+        if (with_cand)
+            cudaMemsetAsync(w.cand_count, 0, sizeof(int) * (nt + 1), s);
+        // own counts, then (FP32 halo path) the per-tile flags and |F| sums behind them
+        cudaMemsetAsync(w.own_count, 0, sizeof(int) * (no + 1 + (with_cand ? 0 : 4 * nt)), s);
+        cudaMemsetAsync(w.counters, 0, sizeof(int) * kCounters, s);
+        IFEM_LAUNCH_CHECK();
+        if (empty)
+            return cudaSuccess;
+        if (with_cand) {
+            bin_kernel<real, false><<<gn, 256, 0, s>>>(b, a.g, w, (const real *)a.x);
+        } else {
+            if constexpr (!std::is_same<real, float>::value)
+                return cudaErrorInvalidValue;   // the one-pass own lists are FP32 only
+            else
+                own_count_kernel<<<g1, 256, 0, s>>>(b, a.g, w, (const float *)a.x);
+        }
+        IFEM_LAUNCH_CHECK();
+        int nb = (int)((no + kScanBlock - 1) / kScanBlock);
+        // without candidate lists the local own offsets go to the cursors, and
+        // own_scatter_kernel writes the final offsets beside them
+        scan_local_kernel<<<nb, kScanThreads, 0, s>>>(with_cand ? nt : 0, no, w.cand_count, w.own_count, w.cand_off,
+                                                      with_cand ? w.own_off : w.own_cursor, w.scan_blocks,
+                                                      w.counters + 8, w.counters + 4);
+        IFEM_LAUNCH_CHECK();
     }
-    IFEM_LAUNCH_CHECK();
-    int nb = (int)((no + kScanBlock - 1) / kScanBlock);
-    // without candidate lists the local own offsets go to the cursors, and
-    // own_scatter_kernel writes the final offsets beside them
-    scan_local_kernel<<<nb, kScanThreads, 0, s>>>(with_cand ? nt : 0, no, w.cand_count, w.own_count, w.cand_off,
-                                                  with_cand ? w.own_off : w.own_cursor, w.scan_blocks,
-                                                  w.counters + 8, w.counters + 4);
-    IFEM_LAUNCH_CHECK();
+    if (empty || !(stages & BIN_PLACE))
+        return cudaSuccess;
     if (with_cand) {
         scan_finish_kernel<<<(unsigned)((no + 1 + 255) / 256), 256, 0, s>>>(nt, no, w);
         IFEM_LAUNCH_CHECK();
@@ -105,7 +112,7 @@ cudaError_t bin_impl(const TransferArgs &a, int det_sort, int with_cand)
         // enough threads for every tile boundary as well as every node
         const long long per_inst = ((nt + 1 + 255) / 256 + b.n_inst - 1) / b.n_inst;
         dim3 gs((unsigned)std::max<long long>(g1.x, per_inst), b.n_inst);
-        own_scatter_kernel<<<gs, 256, 0, s>>>(b, w, nt);
+        own_scatter_kernel<<<gs, 256, 0, s>>>(b, w, nt, (const float *)a.F);
         IFEM_LAUNCH_CHECK();
     }
     if (det_sort) {

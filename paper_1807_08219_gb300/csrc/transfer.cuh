@@ -916,21 +916,63 @@ __host__ __device__ inline int halo_ints(int E)
 // roughly the tile order (in order within each warp's append), so items
 // running at the same time are spatial neighbours whose velocity rows and
 // grid lines share L2 (listing the largest tiles first measured slower).
+// With the forces F given, the placement also sums |F_d| over each tile's
+// own nodes into tile_fsum (zeroed with the counts): the fused transfer's
+// fixed-point scale of item (tile, d) comes from that sum instead of a pass
+// over the item's forces. Lanes of a warp hold consecutive nodes, so the
+// tiles come in runs: a segmented shuffle scan sums each run and its last
+// lane adds it with one atomic per lattice (the order of those atomics is
+// not fixed; the transfer's bound allows for it).
 // Grid: as own_count_kernel along x and y, at least n_tiles + 1 threads in all.
-static __global__ void __launch_bounds__(256) own_scatter_kernel(DevBatch b, DevWork w, long long n_tiles)
+static __global__ void __launch_bounds__(256) own_scatter_kernel(DevBatch b, DevWork w, long long n_tiles,
+                                                                 const float *__restrict__ F)
 {
     const InstDev I = b.inst[blockIdx.y];
+    const long long N = b.N;
+    const int lane = threadIdx.x & 31;
     int node[kBinPer];
     int2 kr[kBinPer];
     float4 rec[kBinPer];
+    float fa[kBinPer][3];
 #pragma unroll
     for (int j = 0; j < kBinPer; ++j) {
         const int k = (blockIdx.x * kBinPer + j) * blockDim.x + threadIdx.x;
         node[j] = I.node_off + k;
         kr[j] = make_int2(-1, 0);
+        fa[j][0] = fa[j][1] = fa[j][2] = 0.f;
         if (k < I.n_nodes) {
             kr[j] = w.node_key[node[j]];
             rec[j] = w.node_rec[node[j]];
+            if (F) {
+                fa[j][0] = fabsf(F[node[j]]);
+                fa[j][1] = fabsf(F[N + node[j]]);
+                fa[j][2] = fabsf(F[2 * N + node[j]]);
+            }
+        }
+    }
+    if (F) {   // the same for every thread of the grid
+#pragma unroll
+        for (int j = 0; j < kBinPer; ++j) {
+            const int tile = kr[j].x >= 0 ? kr[j].x / kOwnSub3 : -1;
+            const int prev = __shfl_up_sync(0xffffffffu, tile, 1);
+            const int next = __shfl_down_sync(0xffffffffu, tile, 1);
+            const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != tile);
+            // first lane of this lane's run
+            const int seg = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const float t = __shfl_up_sync(0xffffffffu, fa[j][d], o);
+                    if (lane - o >= seg)
+                        fa[j][d] += t;
+                }
+            }
+            if (tile >= 0 && (lane == 31 || next != tile)) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    atomicAdd(&w.tile_fsum[3LL * tile + d], fa[j][d]);
+            }
         }
     }
     int off[kBinPer];
@@ -947,7 +989,6 @@ static __global__ void __launch_bounds__(256) own_scatter_kernel(DevBatch b, Dev
     }
     const long long nthr = (long long)gridDim.x * gridDim.y * blockDim.x;
     const long long tid = ((long long)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
     for (long long t0 = tid - lane; t0 <= n_tiles; t0 += nthr) {   // warp-uniform bounds
         const long long t = t0 + lane;
         bool has = false;
@@ -1194,7 +1235,6 @@ __device__ __forceinline__ void pair_stage(const PairItem &it, const float *__re
     }
 }
 
-// sum |F_d| over an item's own nodes, one partial per warp into s_part
 // The first own unit of this thread in an item (node id, binning record,
 // F_d), loaded ahead of the item's node loop.
 struct PairUnit {
@@ -1203,27 +1243,23 @@ struct PairUnit {
     float f;
 };
 
-// sum |F_d| over an item's own nodes, one partial per warp into s_part; the
-// first unit of this thread is returned for the item's node loop.
-__device__ __forceinline__ PairUnit pair_gsum(const PairItem &it, const DevWork &w, const float *__restrict__ F,
-                                              long long N, float *s_part, int lane, int wid)
+// The first unit of this thread for an item's node loop; thread 0 also puts
+// into s_part[0] an upper bound of sum |F_d| over the item's own nodes: the
+// placement's atomic float sum, whose rounding in any order is below
+// (n - 1) 2^-24 of the exact sum for n nodes, times 1.0001 + n 2^-23.
+__device__ __forceinline__ PairUnit pair_first(const PairItem &it, const DevWork &w, const float *__restrict__ F,
+                                               long long N, float *s_part)
 {
     const int beg = w.own_off[(long long)it.tile * kOwnSub3], end = w.own_off[(long long)(it.tile + 1) * kOwnSub3];
     PairUnit u0{0, make_float4(0.f, 0.f, 0.f, 0.f), 0.f};
-    int q = beg + (int)threadIdx.x;
+    const int q = beg + (int)threadIdx.x;
     if (q < end) {
         u0.node = w.own_nodes[q];
         u0.rec = w.own_rec[q];
         u0.f = F[it.d * N + u0.node];
     }
-    float gs = fabsf(u0.f);
-    for (q += blockDim.x; q < end; q += blockDim.x)
-        gs += fabsf(F[it.d * N + w.own_nodes[q]]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        gs += __shfl_down_sync(0xffffffffu, gs, o);
-    if (lane == 0)
-        s_part[wid] = gs;
+    if (threadIdx.x == 0)
+        s_part[0] = w.tile_fsum[3LL * it.tile + it.d] * (1.0001f + (float)(end - beg) * 1.1920929e-7f);
     return u0;
 }
 
@@ -1526,19 +1562,16 @@ __global__ void __launch_bounds__(kStagedThreads, 3) transfer_staged_kernel(DevB
     {
         const PairItem first = pair_item(s_item[0], s_ti[0], s_B[0], density);
         pair_stage(first, u, sU);
-        u0 = pair_gsum(first, w, F, N, s_part, lane, wid);
+        u0 = pair_first(first, w, F, N, s_part);
     }
     cp_async_wait_all();
     __syncthreads();
     for (int slot = 0;; slot ^= 1) {
         const PairItem cur = pair_item(s_item[slot], s_ti[slot], s_B[slot], density);
-        // fixed-point scale of this item from the partial sums of |F_d|
+        // fixed-point scale of this item from the bound of sum |F_d|
         float scale = 1.f;
         {
-            float tot = 0.f;
-            for (int q = 0; q < nw; ++q)
-                tot += s_part[q];
-            const float bound = tot * cur.sd * 0.125f * 1.0001f;
+            const float bound = s_part[0] * cur.sd * 0.125f;
             if (bound > 0.f && isfinite(bound)) {
                 int e = (int)floorf(log2f(FixedPoint<int>::kRange / bound));
                 e = e > 120 ? 120 : (e < -120 ? -120 : e);
@@ -1643,7 +1676,7 @@ __global__ void __launch_bounds__(kStagedThreads, 3) transfer_staged_kernel(DevB
         if (next >= 0) {
             const PairItem nxt = pair_item(next, s_ti[slot ^ 1], s_B[slot ^ 1], density);
             pair_stage(nxt, u, sU);
-            u0 = pair_gsum(nxt, w, F, N, s_part, lane, wid);
+            u0 = pair_first(nxt, w, F, N, s_part);
         }
         {
             const long long n3 = (long long)cur.n * cur.n * cur.n;
