@@ -44,12 +44,11 @@ REF_BUDGET_S = 150.0   # --impl reference: warm-up + timed oracle steps
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the current kernels on the C4 suspension (profiles/*_c4_fp32.md),
 # reported for that workload only; set an entry to None when its kernel changes.
-NCU_TRAFFIC = {"spread+interp": 607.4e6, "spread": None, "interp": None, "forces": None, "bin": None}
+NCU_TRAFFIC = {"spread+interp": None, "spread": None, "interp": None, "forces": None, "bin": None}
 # The unit that bounds each kernel in that capture and its fraction of peak (context for the HBM
 # fraction: the fused transfer kernel is latency-bound at 12 warps per SM, with the L1 load/store
 # pipe the busiest unit; the forces kernel is bound by shared-memory wavefronts).
-NCU_LIMITER = {"spread+interp": ("l1tex load/store data-pipe wavefronts (latency-bound: issue active 33 %)", 0.598),
-               "forces": ("shared-memory wavefronts", 0.598)}
+NCU_LIMITER = {"forces": ("shared-memory wavefronts", 0.598)}
 
 
 def peaks():
