@@ -374,11 +374,14 @@ int ifem_reduce(ifem_ctx ctx, ifem_batch b, const void *x, const void *F, const 
  * the binning and the interpolation beside the spreading, on two streams the
  * context owns, forked from `stream` with events and joined back into it
  * before the reductions (valid under CUDA-graph capture of `stream`); with
- * cfg.profile = 1 the stages run one after the other on `stream` instead, so
- * that ifem_stage_times can attribute them. With IFEM_FP32, IFEM_SCATTER_ATOMIC
+ * cfg.profile = 1 the stages run one after the other on `stream` instead
+ * (forces, then binning, spreading, interpolation, reductions), so that
+ * ifem_stage_times can attribute them. With IFEM_FP32, IFEM_SCATTER_ATOMIC
  * and IFEM_KERNEL_PESKIN4 the interpolation is fused into the spreading
- * kernel (each node's stencil weights serve both transfers); results equal
- * those of the separate calls up to FP32 rounding. */
+ * kernel (each node's stencil weights serve both transfers), and the last
+ * part of the binning waits for the forces: it also sums |F| per tile, which
+ * sets the spread accumulators' fixed-point scales. Results equal those of
+ * the separate calls up to FP32 rounding. */
 int ifem_step_coupling(ifem_ctx ctx, ifem_batch b, ifem_grid g, const void *x, const void *u,
                        void *F, void *f, void *v, double *red, int flags, void *stream);
 
