@@ -1504,14 +1504,15 @@ __global__ void __launch_bounds__(256, 5) spread_halo_kernel(DevBatch b, DevGrid
 // velocity values the item's stencils read (2 cells around the tile), and A,
 // the spread accumulator over the tile plus the halo of spread_halo_kernel
 // (int32 fixed point, scale from the bound sum_k |g_k| / 8 over the tile's
-// own nodes). Per item:
+// own nodes, from the sum of |F_d| that the binning's placement keeps per
+// tile). Per item:
 //   1. node loop, one (node, lattice) unit per thread: the Peskin weights
 //      of the unit; interpolation from U (64 shared-memory loads at
 //      immediate offsets, v_d = sum phi u_d in z-y-x order), then the 64
 //      contributions added to A with shared-memory reductions;
-//   2. the next item's velocity box is copied into U (cp.async) and its
-//      scale bound summed (which also loads each thread's first unit of the
-//      next item) while A is flushed: every non-zero value is added to the
+//   2. the next item's velocity box is copied into U (cp.async), each
+//      thread's first unit of it loaded and its scale bound read, while A
+//      is flushed: every non-zero value is added to the
 //      grid with an L2 reduction (halos of neighbouring tiles combine there)
 //      and cleared.
 // CTAs are small (kStagedThreads): an item has a few hundred units, and the
@@ -1586,7 +1587,7 @@ __global__ void __launch_bounds__(kStagedThreads, 3) transfer_staged_kernel(DevB
         const int end = w.own_off[(long long)(cur.tile + 1) * kOwnSub3];
         const int px = cur.px, pp = cur.pp;
         // 1. node loop: one (node, lattice) unit per thread; the first unit
-        // was loaded with the scale sum
+        // was loaded ahead (pair_first)
         PairUnit un = u0;
         for (int q = beg + (int)threadIdx.x; q < end;) {
             const int node = un.node;
